@@ -1,0 +1,521 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these checks re-types an oracle formula: each compares the oracle with an independent
+fact (finite differences, closed-form stationary moments, a library log-density, a published
+known-answer vector, the prefix-exactness and <= T convergence properties of Newton's method).
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle as O
+import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ------------------------------------------------------------------------------------------
+# helpers
+# ------------------------------------------------------------------------------------------
+
+def fd_jac(fun, x, h=1e-6):
+    """Central finite-difference Jacobian of fun: R^n -> R^m at x."""
+    x = np.asarray(x, dtype=np.float64)
+    cols = []
+    for j in range(x.size):
+        hj = h * (1.0 + abs(x[j]))
+        e = np.zeros_like(x)
+        e[j] = hj
+        cols.append((np.asarray(fun(x + e)) - np.asarray(fun(x - e))) / (2 * hj))
+    return np.stack(cols, axis=-1)
+
+
+def small_logreg(N=40, D=3, seed=3, sigma_p=1.3):
+    X, y, _ = W.blr_data(N, D, seed=seed)
+    return O.Target("logreg", D, X=X, y=y, sigma_p=sigma_p)
+
+
+def gauss(D=3, seed=5):
+    cov, prec, _ = W.random_spd(D, seed=seed)
+    mu = np.random.default_rng(seed).standard_normal(D)
+    return O.Target("gaussian", D, mu=mu, P=prec), mu, cov
+
+
+def batch_means_se(x, nb=50):
+    """Standard error of the mean of an autocorrelated series by batch means."""
+    n = len(x) // nb * nb
+    b = x[:n].reshape(nb, -1).mean(axis=1)
+    return b.std(ddof=1) / np.sqrt(nb)
+
+
+# ------------------------------------------------------------------------------------------
+# Philox and noise
+# ------------------------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    path = os.path.join(HERE, "golden", "philox4x32_10_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(v, 16) for v in r]
+        out = O.philox4x32_10(w[0:4], w[4:6])
+        assert list(out) == w[6:10]
+
+
+def test_noise_distribution():
+    xi, u = O.gen_noise(seed=12345, chain_id=7, T=40000, D=3)
+    assert np.all(u > 0) and np.all(u < 1)
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+    for d in range(3):
+        assert stats.kstest(xi[:, d], "norm").pvalue > 1e-4
+    # the two Box-Muller outputs of one pair are uncorrelated
+    assert abs(np.corrcoef(xi[:, 0], xi[:, 1])[0, 1]) < 0.03
+
+
+def test_noise_counters_are_per_chain_and_step():
+    xi1, u1 = O.gen_noise(seed=1, chain_id=0, T=8, D=4)
+    xi2, u2 = O.gen_noise(seed=1, chain_id=0, T=16, D=4)
+    np.testing.assert_array_equal(xi1, xi2[:8])        # prefix-stable in T
+    np.testing.assert_array_equal(u1, u2[:8])
+    xi3, _ = O.gen_noise(seed=1, chain_id=1, T=8, D=4)
+    assert not np.allclose(xi1, xi3)
+    xi4, _ = O.gen_noise(seed=1, chain_id=0, T=8, D=3)
+    np.testing.assert_array_equal(xi4, xi1[:, :3])     # prefix-stable in D
+
+
+# ------------------------------------------------------------------------------------------
+# Targets (L0)
+# ------------------------------------------------------------------------------------------
+
+def test_gaussian_logp_matches_scipy():
+    t, mu, cov = gauss(D=4)
+    mvn = stats.multivariate_normal(mu, cov)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        a, b = rng.standard_normal(4), rng.standard_normal(4)
+        assert O.logp(t, a) - O.logp(t, b) == pytest.approx(mvn.logpdf(a) - mvn.logpdf(b),
+                                                            rel=1e-12, abs=1e-12)
+
+
+def test_logreg_logp_matches_bernoulli_likelihood():
+    X, y, _ = W.blr_data(60, 4, seed=1)
+    sp = 1.7
+    t = O.Target("logreg", 4, X=X, y=y, sigma_p=sp)
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        a, b = rng.standard_normal(4), rng.standard_normal(4)
+
+        def lp(w):
+            p = 1.0 / (1.0 + np.exp(-(X @ w)))
+            return stats.bernoulli.logpmf(y, p).sum() + stats.norm.logpdf(w, 0, sp).sum()
+
+        assert O.logp(t, a) - O.logp(t, b) == pytest.approx(lp(a) - lp(b), rel=1e-10, abs=1e-10)
+
+
+def test_banana_closed_form_points():
+    t = O.Target("banana", 2)
+    # log p = -x1^2/200 - (x2 + 0.1 x1^2 - 10)^2/2 has its maximum 0 on x = (0, 10)
+    assert O.logp(t, [0.0, 10.0]) == 0.0
+    assert O.logp(t, [10.0, 0.0]) == pytest.approx(-0.5)        # b = 0
+    assert O.logp(t, [0.0, 0.0]) == pytest.approx(-50.0)        # b = -10
+    np.testing.assert_allclose(O.grad(t, [0.0, 10.0]), [0.0, 0.0], atol=0)
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "logreg", "banana"])
+def test_gradient_and_hessian_match_finite_differences(kind):
+    if kind == "gaussian":
+        t = gauss(D=4)[0]
+    elif kind == "logreg":
+        t = small_logreg(N=80, D=4)
+    else:
+        t = O.Target("banana", 2)
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        x = rng.standard_normal(t.D) * (3.0 if kind == "banana" else 0.7)
+        g_fd = fd_jac(lambda z: np.array([O.logp(t, z)]), x)[0]
+        np.testing.assert_allclose(O.grad(t, x), g_fd, rtol=1e-6, atol=1e-6)
+        H_fd = fd_jac(lambda z: O.grad(t, z), x)
+        np.testing.assert_allclose(O.hess(t, x), H_fd, rtol=1e-6, atol=1e-6)
+
+
+# ------------------------------------------------------------------------------------------
+# Transitions (L1)
+# ------------------------------------------------------------------------------------------
+
+def test_mala_ratio_matches_library_proposal_densities():
+    """ell = log p(x~) + log q(x|x~) - log p(x) - log q(x~|x), q = N(b + eps grad(b), 2 eps I)."""
+    t = small_logreg(N=50, D=3)
+    eps = 0.05
+    rng = np.random.default_rng(4)
+    for _ in range(6):
+        x, xi = rng.standard_normal(3) * 0.5, rng.standard_normal(3)
+        xt = x + eps * O.grad(t, x) + np.sqrt(2 * eps) * xi
+        cov = 2 * eps * np.eye(3)
+        ref = (O.logp(t, xt) - O.logp(t, x)
+               + stats.multivariate_normal(xt + eps * O.grad(t, xt), cov).logpdf(x)
+               - stats.multivariate_normal(x + eps * O.grad(t, x), cov).logpdf(xt))
+        _, ell, _ = O.mala_step(t, eps, x, xi, 0.5)
+        assert ell == pytest.approx(ref, rel=1e-10, abs=1e-10)
+        # the proposal is the ULA step
+        np.testing.assert_allclose(O.mala_step(t, eps, x, xi, 0.5, mh=False)[0], xt, rtol=1e-14)
+
+
+def test_mala_accepts_strictly_above_log_u():
+    t = gauss(D=2)[0]
+    x, xi = np.array([1.5, -0.7]), np.array([0.3, 2.0])
+    _, ell, _ = O.mala_step(t, 0.3, x, xi, 0.5)
+    assert ell < 0
+    u_lo, u_hi = np.exp(ell) * (1 - 1e-9), np.exp(ell) * (1 + 1e-9)
+    assert O.mala_step(t, 0.3, x, xi, u_lo)[2]
+    assert not O.mala_step(t, 0.3, x, xi, u_hi)[2]
+    np.testing.assert_array_equal(O.mala_step(t, 0.3, x, xi, u_hi)[0], x)
+
+
+def _long_chain(sampler, target, eps, T, L=0, seed=0):
+    xi, u = W.noise(T, target.D, seed=seed)
+    p = O.Problem(target, sampler, eps, xi=xi, u=u, L=L)
+    s, _, acc = O.chain(p, T, np.zeros(target.D))
+    return s, acc
+
+
+@pytest.mark.parametrize("sampler,eps,L", [("mala", 0.1, 0), ("hmc", 0.1, 10)])
+def test_gaussian_chain_has_target_moments(sampler, eps, L):
+    """MALA and HMC leave N(0, Sigma) invariant: the chain's mean and covariance match."""
+    mu, prec, cov = W.gaussian_c1()
+    t = O.Target("gaussian", 2, mu=mu, P=prec)
+    s, acc = _long_chain(sampler, t, eps, 200_000, L=L, seed=7)
+    s = s[2000:]
+    for d in range(2):
+        assert abs(s[:, d].mean()) < 5 * batch_means_se(s[:, d]) + 1e-3
+        v = (s[:, d] - 0.0) ** 2
+        assert abs(v.mean() - cov[d, d]) < 5 * batch_means_se(v) + 1e-3
+    cxy = s[:, 0] * s[:, 1]
+    assert abs(cxy.mean() - cov[0, 1]) < 5 * batch_means_se(cxy) + 1e-3
+
+
+def test_ula_chain_has_closed_form_covariance():
+    """Without the MH step the Gaussian chain is affine; in the eigenbasis of P its stationary
+    variance is 2 eps / (1 - (1 - eps lam)^2), which differs from 1/lam (Section 2's affine
+    case).  This pins the proposal and separates MALA from ULA."""
+    mu, prec, cov = W.gaussian_c1()
+    t = O.Target("gaussian", 2, mu=mu, P=prec)
+    eps = 0.1
+    s, _ = _long_chain("ula", t, eps, 200_000, seed=9)
+    lam, Q = np.linalg.eigh(prec)
+    z = s[2000:] @ Q
+    for i in range(2):
+        expected = 2 * eps / (1 - (1 - eps * lam[i]) ** 2)
+        v = z[:, i] ** 2
+        assert abs(v.mean() - expected) < 5 * batch_means_se(v) + 1e-3
+    assert abs(2 * eps / (1 - (1 - eps * lam[1]) ** 2) - 1 / lam[1]) > 0.05
+
+
+def test_banana_hmc_moments():
+    """x1 ~ N(0, 100), x2 | x1 ~ N(10 - 0.1 x1^2, 1): E x2 = 0, Var x1 = 100, Var x2 = 201."""
+    t = O.Target("banana", 2)
+    s, acc = _long_chain("hmc", t, 0.2, 200_000, L=50, seed=2)
+    s = s[5000:]
+    assert acc.mean() > 0.5
+    m1, m2 = s[:, 0].mean(), s[:, 1].mean()
+    assert abs(m1) < 5 * batch_means_se(s[:, 0]) + 0.1
+    assert abs(m2) < 5 * batch_means_se(s[:, 1]) + 0.1
+    v1 = s[:, 0] ** 2
+    assert abs(v1.mean() - 100) < 5 * batch_means_se(v1) + 1.0
+    v2 = (s[:, 1]) ** 2
+    assert abs(v2.mean() - 201) < 5 * batch_means_se(v2) + 2.0
+
+
+def test_leapfrog_is_eq7():
+    """Two leapfrog steps composed agree with the symplectic-Euler map of Eq. 7 applied twice,
+    and its Jacobian has unit determinant (volume preservation)."""
+    t = O.Target("banana", 2)
+    s = np.array([1.2, 3.4, -0.3, 0.8])
+    J = fd_jac(lambda z: O.leapfrog(t, 0.05, z), s)
+    assert np.linalg.det(J) == pytest.approx(1.0, abs=1e-8)
+    xp = s[:2] + 0.05 * s[2:]
+    np.testing.assert_allclose(O.leapfrog(t, 0.05, s)[:2], xp, rtol=1e-15)
+
+
+# ------------------------------------------------------------------------------------------
+# Newton Jacobians (L2)
+# ------------------------------------------------------------------------------------------
+
+def _sig(z):
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def _mala_pieces(t, eps, xi, u):
+    def prop(x):
+        return O.mala_step(t, eps, x, xi, u, mh=False)[0]
+
+    def gtilde(x):
+        _, ell, _ = O.mala_step(t, eps, x, xi, u)
+        return min(0.0, ell) - np.log(u)
+
+    return prop, gtilde
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "logreg", "banana"])
+def test_mala_jacobian_is_stop_gradient_relaxation(kind):
+    """J_sg = d/dx[sigma(g~) x~ + (1 - sigma(g~)) x] + (1(g~>0) - sigma(g~)) (dx~/dx - I)."""
+    if kind == "gaussian":
+        t = gauss(D=3)[0]
+    elif kind == "logreg":
+        t = small_logreg(N=40, D=3)
+    else:
+        t = O.Target("banana", 2)
+    eps = 0.2 if kind != "logreg" else 0.3
+    rng = np.random.default_rng(21)
+    n_active = 0
+    for trial in range(60):
+        if n_active >= 4:
+            break
+        x = rng.standard_normal(t.D)
+        if kind == "banana":        # start on the ridge x2 = 10 - 0.1 x1^2 of the target
+            x = np.array([3 * x[0], 10 - 0.3 * x[0] ** 2 + x[1]])
+        xi = rng.standard_normal(t.D)
+        u = rng.uniform(0.05, 0.95)
+        prop, gtilde = _mala_pieces(t, eps, xi, u)
+        g0 = gtilde(x)
+        _, ell, acc = O.mala_step(t, eps, x, xi, u)
+        if abs(ell) < 1e-3 or abs(g0) < 1e-3:
+            continue
+        n_active += ell < 0
+        relaxed = lambda z: _sig(gtilde(z)) * prop(z) + (1 - _sig(gtilde(z))) * z
+        Jr = fd_jac(relaxed, x)
+        Jp = fd_jac(prop, x)
+        expected = Jr + (float(acc) - _sig(g0)) * (Jp - np.eye(t.D))
+        p = O.Problem(t, "mala", eps, xi=xi[None, :], u=np.array([u]))
+        J = O.jacobian(p, 1, x, "dense")
+        np.testing.assert_allclose(J, expected, rtol=1e-5, atol=1e-6)
+        # the held-gate Jacobian drops only the sigma' term
+        p0 = O.Problem(t, "mala", eps, xi=xi[None, :], u=np.array([u]), gate_grad=0)
+        J0 = O.jacobian(p0, 1, x, "dense")
+        np.testing.assert_allclose(J0, float(acc) * Jp + (1 - float(acc)) * np.eye(t.D),
+                                   rtol=1e-5, atol=1e-6)
+    assert n_active >= 2
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "banana", "logreg"])
+def test_hmc_jacobian_is_stop_gradient_relaxation(kind):
+    if kind == "gaussian":
+        t = gauss(D=3)[0]
+        eps, L = 0.2, 5
+    elif kind == "logreg":
+        t = small_logreg(N=30, D=3)
+        eps, L = 0.05, 4
+    else:
+        t = O.Target("banana", 2)
+        eps, L = 0.05, 16
+    rng = np.random.default_rng(8)
+    n_active = 0
+    for trial in range(60):
+        if n_active >= 4:
+            break
+        x = rng.standard_normal(t.D)
+        if kind == "banana":        # start on the ridge x2 = 10 - 0.1 x1^2 of the target
+            x = np.array([3 * x[0], 10 - 0.3 * x[0] ** 2 + x[1]])
+        xi = rng.standard_normal(t.D)
+        u = rng.uniform(0.05, 0.95)
+
+        def prop(z):
+            return O.hmc_step(t, eps, L, z, xi, 1e-300)[0]
+
+        def gtilde(z):
+            return min(0.0, O.hmc_step(t, eps, L, z, xi, u)[1]) - np.log(u)
+
+        _, dH, acc = O.hmc_step(t, eps, L, x, xi, u)
+        g0 = gtilde(x)
+        if abs(dH) < 1e-3 or abs(g0) < 1e-3:
+            continue
+        n_active += dH < 0
+        relaxed = lambda z: _sig(gtilde(z)) * prop(z) + (1 - _sig(gtilde(z))) * z
+        expected = fd_jac(relaxed, x) + (float(acc) - _sig(g0)) * (fd_jac(prop, x) - np.eye(t.D))
+        p = O.Problem(t, "hmc", eps, xi=xi[None, :], u=np.array([u]), L=L)
+        np.testing.assert_allclose(O.jacobian(p, 1, x, "dense"), expected, rtol=1e-5, atol=1e-6)
+    assert n_active >= 2
+
+
+def test_leapfrog_jacobian_and_block_form():
+    t = small_logreg(N=30, D=3)
+    p = O.Problem(t, "leapfrog", 0.07)
+    s = np.random.default_rng(1).standard_normal(6)
+    J = O.jacobian(p, 1, s, "dense")
+    np.testing.assert_allclose(J, fd_jac(lambda z: O.leapfrog(t, 0.07, z), s), rtol=1e-6, atol=1e-7)
+    Jb = O.jacobian(p, 1, s, "block2")
+    # block quasi-DEER keeps exactly the diagonal of each D x D block (Appendix A.3)
+    mask = np.zeros((6, 6), bool)
+    for i in range(6):
+        for j in range(6):
+            mask[i, j] = (i % 3) == (j % 3)
+    np.testing.assert_array_equal(Jb[mask], J[mask])
+    assert np.all(Jb[~mask] == 0)
+    Jd = O.jacobian(p, 1, s, "diag")
+    np.testing.assert_array_equal(np.diag(Jd), np.diag(J))
+    assert np.count_nonzero(Jd - np.diag(np.diag(Jd))) == 0
+
+
+def test_damping_and_clip():
+    t = O.Target("banana", 2)
+    xi, u = np.array([[0.4, -1.0]]), np.array([0.3])
+    x = np.array([4.0, -3.0])
+    J = O.jacobian(O.Problem(t, "hmc", 0.05, xi=xi, u=u, L=16), 1, x, "dense")
+    Jc = O.jacobian(O.Problem(t, "hmc", 0.05, xi=xi, u=u, L=16, damping=0.5, clip=1), 1, x, "dense")
+    np.testing.assert_allclose(Jc, np.clip(0.5 * J, -1, 1), rtol=1e-15)
+
+
+def test_block_composition_formula():
+    """Appendix A.3: the product of two 2x2-block matrices with diagonal blocks has diagonal
+    blocks (ae+bg, af+bh; ce+dg, cf+dh) -- 8 elementwise products."""
+    rng = np.random.default_rng(0)
+    D = 5
+    a, b, c, d, e, f, g, h = rng.standard_normal((8, D))
+    A = np.block([[np.diag(a), np.diag(b)], [np.diag(c), np.diag(d)]])
+    B = np.block([[np.diag(e), np.diag(f)], [np.diag(g), np.diag(h)]])
+    AB = A @ B
+    np.testing.assert_allclose(np.diag(AB[:D, :D]), a * e + b * g, rtol=1e-14)
+    np.testing.assert_allclose(np.diag(AB[:D, D:]), a * f + b * h, rtol=1e-14)
+    np.testing.assert_allclose(np.diag(AB[D:, :D]), c * e + d * g, rtol=1e-14)
+    np.testing.assert_allclose(np.diag(AB[D:, D:]), c * f + d * h, rtol=1e-14)
+    off = AB.copy()
+    for i in range(2 * D):
+        for j in range(2 * D):
+            if i % D == j % D:
+                off[i, j] = 0
+    assert np.abs(off).max() == 0
+
+
+# ------------------------------------------------------------------------------------------
+# DEER: convergence to the sequential trace, prefix exactness, <= T iterations
+# ------------------------------------------------------------------------------------------
+
+def _problem(kind, T, seed=0):
+    if kind == "mala_gauss":
+        mu, prec, _ = W.gaussian_c1()
+        t = O.Target("gaussian", 2, mu=mu, P=prec)
+        xi, u = W.noise(T, 2, seed=seed)
+        return O.Problem(t, "mala", 0.1, xi=xi, u=u), np.zeros(2)
+    if kind == "mala_logreg":
+        t = small_logreg(N=60, D=4, sigma_p=1.0)
+        xi, u = W.noise(T, 4, seed=seed)
+        return O.Problem(t, "mala", 0.02, xi=xi, u=u), np.zeros(4)
+    if kind == "hmc_banana":
+        t = O.Target("banana", 2)
+        xi, u = W.noise(T, 2, seed=seed)
+        return O.Problem(t, "hmc", 0.05, xi=xi, u=u, L=16), np.zeros(2)
+    if kind == "leapfrog_logreg":
+        t = small_logreg(N=60, D=4, sigma_p=1.0)
+        return O.Problem(t, "leapfrog", 0.05), np.random.default_rng(1).standard_normal(8)
+    raise KeyError(kind)
+
+
+@pytest.mark.parametrize("kind,jac", [
+    ("mala_gauss", "dense"), ("mala_gauss", "diag"), ("mala_gauss", "zero"),
+    ("mala_logreg", "diag"), ("mala_logreg", "dense"), ("hmc_banana", "diag"),
+    ("hmc_banana", "dense"), ("leapfrog_logreg", "block2"), ("leapfrog_logreg", "diag"),
+])
+def test_deer_reaches_sequential_trace(kind, jac):
+    T = 48
+    p, s0 = _problem(kind, T)
+    ref, _, _ = O.chain(p, T, s0)
+    s, iters, conv, hist = O.deer(p, T, s0, kind=jac, atol=1e-11)
+    assert conv
+    assert iters <= T
+    np.testing.assert_allclose(s, ref, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind,jac", [("mala_gauss", "diag"), ("hmc_banana", "diag"),
+                                      ("mala_logreg", "dense"), ("leapfrog_logreg", "block2")])
+def test_deer_prefix_is_exact_after_k_iterations(kind, jac):
+    """After k Newton updates from any guess, s_1..s_k equal the sequential trace (Section 2:
+    s_1 = f_1(s_0) is exact after one update, and induction)."""
+    T = 24
+    p, s0 = _problem(kind, T, seed=3)
+    ref, _, _ = O.chain(p, T, s0)
+    for k in range(1, 8):
+        s, iters, _, _ = O.deer(p, T, s0, kind=jac, max_iters=k, atol=-1.0)
+        assert iters == k
+        np.testing.assert_allclose(s[:k], ref[:k], rtol=1e-11, atol=1e-11)
+
+
+def test_dense_deer_solves_affine_chain_in_one_update():
+    """ULA on a Gaussian is affine, so the exact-Jacobian Newton step is exact (Section 2)."""
+    _, prec, _ = W.gaussian_c1()
+    t = O.Target("gaussian", 2, mu=np.array([0.3, -0.2]), P=prec)
+    T = 200
+    xi, u = W.noise(T, 2, seed=4)
+    p = O.Problem(t, "ula", 0.1, xi=xi, u=u)
+    s, iters, conv, hist = O.deer(p, T, np.zeros(2), kind="dense", atol=1e-12)
+    assert conv and iters == 1
+    ref, _, _ = O.chain(p, T, np.zeros(2))
+    np.testing.assert_allclose(s, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_picard_and_newton_agree_with_each_other():
+    """The J = 0 fixed-point iteration and DEER reach the same trace on tiny T (brute force)."""
+    T = 12
+    p, s0 = _problem("hmc_banana", T, seed=5)
+    a, ia, ca, _ = O.deer(p, T, s0, kind="zero", atol=1e-12)
+    b, ib, cb, _ = O.deer(p, T, s0, kind="dense", atol=1e-12)
+    assert ca and cb and ia <= T and ib <= T
+    np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-10)
+
+
+def test_step_rule_of_algorithm_1():
+    T = 32
+    p, s0 = _problem("mala_gauss", T)
+    s, it, conv, _ = O.deer(p, T, s0, kind="dense", atol=1e-12, rule="step")
+    ref, _, _ = O.chain(p, T, s0)
+    assert conv
+    np.testing.assert_allclose(s, ref, rtol=1e-10, atol=1e-10)
+
+
+# ------------------------------------------------------------------------------------------
+# Adjoint with decisions held
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("sp", [1.0, 1.6])
+def test_adjoint_matches_frozen_finite_differences(sp):
+    T, D = 40, 3
+    t = small_logreg(N=30, D=D, sigma_p=sp)
+    xi, u = W.noise(T, D, seed=6)
+    eps = 0.03
+    s0 = np.zeros(D)
+    p = O.Problem(t, "mala", eps, xi=xi, u=u)
+    s, _, acc = O.chain(p, T, s0)
+    assert 0 < acc.mean() < 1
+    dLds = 2.0 * s / T                     # L = mean_t |s_t|^2
+    g = O.mala_adjoint(p, T, s0, s, acc, dLds)
+
+    def L_of(e, spv):
+        tt = O.Target("logreg", D, X=t.X, y=t.y, sigma_p=spv)
+        pp = O.Problem(tt, "mala", e, xi=xi, u=u)
+        ss = O.mala_chain_frozen(pp, T, s0, acc)
+        return (ss ** 2).sum() / T
+
+    h = 1e-4
+    fd_e = (L_of(eps + h * eps, sp) - L_of(eps - h * eps, sp)) / (2 * h * eps)
+    fd_s = (L_of(eps, sp + h) - L_of(eps, sp - h)) / (2 * h)
+    assert g[0] == pytest.approx(fd_e, rel=1e-5)
+    assert g[1] == pytest.approx(fd_s, rel=1e-5)
+    # the frozen chain at the original parameters is the chain itself
+    np.testing.assert_allclose(O.mala_chain_frozen(p, T, s0, acc), s, rtol=1e-14)
+
+
+def test_non_finite_proposal_rejects_and_deer_does_not_stop_on_nan():
+    """min(0, NaN) propagates NaN, so a divergent proposal rejects; a NaN iterate is never
+    reported as converged, and Newton still reaches the trace in <= T updates."""
+    t = O.Target("banana", 2)
+    x = np.array([1e200, 1.0])
+    out, dH, acc = O.hmc_step(t, 0.05, 4, x, np.array([0.1, 0.2]), 0.5)
+    assert not acc and np.isnan(dH)
+    np.testing.assert_array_equal(out, x)
+    T = 60
+    p, s0 = _problem("hmc_banana", T, seed=0)
+    ref, _, _ = O.chain(p, T, s0)
+    s, iters, conv, hist = O.deer(p, T, s0, kind="diag", atol=1e-10)   # undamped: blows up
+    assert conv and iters <= T and not np.isnan(s).any()
+    assert np.isinf(hist).any()
+    np.testing.assert_allclose(s, ref, rtol=1e-9, atol=1e-9)
