@@ -1,0 +1,238 @@
+/*
+ * pmcmc.h -- C ABI of a single-GPU (GB300, sm_103a) parallel-Newton MCMC solver.
+ *
+ * The library evaluates an MCMC chain s_1..s_T in parallel across its length, following
+ * "Parallelizing MCMC Across the Sequence Length" (arXiv 2508.18413).  With the per-step noise
+ * (xi_t, u_t) fixed, the chain is the fixed point of s_t = f_t(s_{t-1}) (Section 2, Section 3).
+ * Each Newton iteration (Algorithm 1)
+ *   (a) evaluates f_t and a Jacobian J_t at the previous iterate for all t at once
+ *       (Eq. 2: dense J = DEER; Eq. 4: diagonal = quasi-DEER; Appendix A.3: block quasi-DEER),
+ *   (b) solves the linearised recursion delta_t = J_t delta_{t-1} + r_t,
+ *       r_t = f_t(s_{t-1}) - s_t, with a single-pass parallel scan over affine maps (Section 2),
+ *       and sets s <- s + delta (algebraically Eq. 3),
+ *   (c) stops when the residual of Eq. 1 meets the tolerance.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" must be device memory of the context's GPU; "host" pointers are
+ *     ordinary host memory.  The caller owns every buffer it passes; the library owns only its
+ *     internal workspace (allocated lazily, reused, freed by pmcmc_destroy).
+ *   - Real-valued device buffers hold double for PMCMC_F64 and float for the FP32 precisions,
+ *     except u (the accept uniforms), which is always double.  Arrays are row-major with the
+ *     time index slowest: s[t][d] is s + t*D + d for t = 0..T-1 (t = 0 is step 1).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is stream-ordered;
+ *     calls that fill a host result struct synchronise that stream before returning.
+ *   - Errors are returned as pmcmc_status; nothing is thrown across the ABI.  After a negative
+ *     status, pmcmc_last_error() describes the failure.  A context is not thread-safe: use one
+ *     context per host thread.
+ */
+#ifndef PMCMC_H
+#define PMCMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmcmc_ctx pmcmc_ctx;
+
+typedef enum {
+    PMCMC_OK = 0,
+    PMCMC_NOT_CONVERGED = 1, /* max_iters reached; the last iterate is still written (early
+                                stopping, Section 3.4) */
+    PMCMC_EINVAL = -1,       /* invalid argument (sizes, NULL pointers, unsupported combination) */
+    PMCMC_ENOMEM = -2,       /* workspace allocation failed */
+    PMCMC_ECUDA = -3,        /* a CUDA call failed */
+    PMCMC_ETIMEOUT = -4,     /* a bounded device-side wait ran out (scan look-back) */
+    PMCMC_ENAN = -5,         /* the initial state or data is not finite */
+    PMCMC_EUNSUPPORTED = -6  /* a size beyond what the kernels are compiled for */
+} pmcmc_status;
+
+/* f_t: the sampler transition (Section 3.2 MALA; Algorithm 2 HMC with a sequential leapfrog;
+ * HMC with the leapfrog itself solved by block quasi-DEER, Section 3.3). */
+typedef enum { PMCMC_MALA = 0, PMCMC_HMC = 1, PMCMC_HMC_PAR_LEAPFROG = 2 } pmcmc_sampler;
+
+/* Built-in target densities (log p up to a constant):
+ *   GAUSSIAN: -1/2 (x - mean)^T prec (x - mean)
+ *   LOGREG:   sum_n [y_n z_n - log(1 + exp z_n)] - |x|^2 / (2 prior_scale^2),  z = X x
+ *   BANANA:   -x1^2/200 - (x2 + 0.1 x1^2 - 10)^2 / 2   (D = 2) */
+typedef enum { PMCMC_GAUSSIAN = 0, PMCMC_LOGREG = 1, PMCMC_BANANA = 2 } pmcmc_target_kind;
+
+/* Newton Jacobian used in step (a):
+ *   DENSE      the full stop-gradient Jacobian (DEER, Eq. 2);
+ *   DIAG       its exact diagonal (quasi-DEER, Eq. 4);
+ *   BLOCK2     diagonal of each block of the leapfrog Jacobian (Appendix A.3; only
+ *              PMCMC_HMC_PAR_LEAPFROG);
+ *   DIAG_HUTCH one-sample Hutchinson estimate z (.) (J z), z Rademacher (Eq. 9);
+ *   ZERO       J = 0: the plain fixed-point (Picard-type) iteration. */
+typedef enum {
+    PMCMC_JAC_DENSE = 0,
+    PMCMC_JAC_DIAG = 1,
+    PMCMC_JAC_BLOCK2 = 2,
+    PMCMC_JAC_DIAG_HUTCH = 3,
+    PMCMC_JAC_ZERO = 4
+} pmcmc_jac;
+
+/* Arithmetic: F64 everywhere; F32 states/f/J with the MH log-ratio accumulated and compared
+ * in FP64; F32_SCAN_BF16 as F32 but the scan's affine pairs (J_t, r_t) stored as bfloat16 and
+ * combined in FP32 (the Newton loop refines the solve; r_t is always formed in FP32). */
+typedef enum { PMCMC_F64 = 0, PMCMC_F32 = 1, PMCMC_F32_SCAN_BF16 = 2 } pmcmc_precision;
+
+typedef struct {
+    pmcmc_target_kind kind;
+    int D;               /* dimension of x */
+    int N;               /* LOGREG: number of rows of X */
+    const void *mean;    /* GAUSSIAN: D reals, device */
+    const void *prec;    /* GAUSSIAN: D x D precision matrix (symmetric), row-major, device */
+    const void *X;       /* LOGREG: N x D design, row-major, device */
+    const void *y;       /* LOGREG: N labels in {0, 1}, reals, device */
+    double prior_scale;  /* LOGREG: prior N(0, prior_scale^2 I) */
+} pmcmc_target;
+
+typedef struct {
+    pmcmc_sampler sampler;
+    double step;          /* step size epsilon */
+    int leapfrog_L;       /* leapfrog steps per HMC transition */
+    pmcmc_jac jac;
+    pmcmc_precision precision;
+    double atol, rtol;    /* converged when max_{t,d} (|r_td| - rtol |s_td|) <= atol (App. B) */
+    int max_iters;        /* Newton updates allowed; <= 0 means T (the proven bound) */
+    double damping;       /* J <- damping J before clipping; 0 means 1 (App. B.4) */
+    int clip;             /* 1: clip entries of J to [-1, 1] (App. B.4) */
+    int gate_grad;        /* 1: J carries the stop-gradient gate term of Section 3.2 */
+    unsigned long long seed; /* noise seed when xi/u are NULL, and for Hutchinson probes */
+    unsigned int chain_id;   /* noise counter of this chain */
+    int spin_limit;       /* look-back wait bound (polls); 0 = default */
+} pmcmc_options;
+
+typedef struct {
+    int iters;            /* Newton updates applied */
+    int status;           /* pmcmc_status of the solve */
+    double max_residual;  /* max_{t,d} |r_td| of the returned iterate */
+    double accept_rate;   /* fraction of accepted MH steps in the returned iterate */
+    double min_margin;    /* min_t |log alpha_t - log u_t| of the returned iterate */
+    int nonfinite_resets; /* elements of an iterate that were non-finite and were reset */
+    float elapsed_ms;     /* device time of the solve (CUDA events) */
+} pmcmc_result;
+
+/* Fill `opt` with defaults: MALA, step 0.01, DIAG, F32, atol 1e-5, rtol 0, max_iters T,
+ * damping 1, no clip, gate_grad 1, seed 0, chain 0. */
+void pmcmc_options_default(pmcmc_options *opt);
+
+/* Create a context on CUDA device `device`.  Returns EINVAL/ECUDA on failure. */
+pmcmc_status pmcmc_create(pmcmc_ctx **ctx, int device);
+
+/* Free the context and its workspace.  NULL is accepted. */
+pmcmc_status pmcmc_destroy(pmcmc_ctx *ctx);
+
+/* Text of the last error on this context (static storage owned by the context). */
+const char *pmcmc_last_error(pmcmc_ctx *ctx);
+
+/*
+ * Counter-based noise (Section 3.2: xi_t ~ N(0, I), u_t ~ U(0, 1) are inputs of f_t).
+ * Philox4x32-10 keyed by the 64-bit seed; xi[t][2j], xi[t][2j+1] are the Box-Muller pair of
+ * the two 53-bit uniforms of counter (j, t, chain_id, 0); u[t] is the first 53-bit uniform of
+ * counter (0, t, chain_id, 1); uniforms are (k + 1/2) 2^-53.
+ *   xi: T x D device reals of `precision` (may be NULL); u: T device doubles (may be NULL).
+ */
+pmcmc_status pmcmc_gen_noise(pmcmc_ctx *ctx, unsigned long long seed, unsigned int chain_id,
+                             int T, int D, pmcmc_precision precision, void *xi, double *u,
+                             void *stream);
+
+/*
+ * Parallel Newton solve of the chain (Algorithm 1 with the update of Eq. 2/3/4).
+ *   s0:     D device reals, the given initial state (Section 2).
+ *   s_init: T x D device reals, the initial guess s^(0); NULL means s^(0)_t = s0 for all t
+ *           (Appendix B).  Passing any iterate resumes from it.
+ *   xi, u:  T x D device reals and T device doubles of noise; both NULL means generated from
+ *           (opt->seed, opt->chain_id) as pmcmc_gen_noise does.
+ *   s_out:  T x D device reals, written with the returned iterate (also when NOT_CONVERGED).
+ *   res:    host struct filled on return (may be NULL).
+ * For PMCMC_HMC_PAR_LEAPFROG the chain is solved step by step and each step's L leapfrog
+ * updates are solved by block quasi-DEER (Algorithm 2); opt->max_iters then bounds the inner
+ * Newton iterations per step (<= 0 means L).
+ * Returns OK, NOT_CONVERGED or an error.
+ */
+pmcmc_status pmcmc_solve(pmcmc_ctx *ctx, const pmcmc_target *target, const pmcmc_options *opt,
+                         int T, const void *s0, const void *s_init, const void *xi,
+                         const double *u, void *s_out, pmcmc_result *res, void *stream);
+
+/*
+ * The sequential chain s_t = f_t(s_{t-1}) on the GPU (the paper's sequential baseline,
+ * Section 5: one dependent step after another).  Same arguments as pmcmc_solve without the
+ * Newton controls.  accept_out (T bytes, device, may be NULL) receives the decisions.
+ */
+pmcmc_status pmcmc_seq_solve(pmcmc_ctx *ctx, const pmcmc_target *target,
+                             const pmcmc_options *opt, int T, const void *s0, const void *xi,
+                             const double *u, void *s_out, unsigned char *accept_out,
+                             void *stream);
+
+/*
+ * One evaluate-and-linearise pass (step (a)) at a given trajectory s (T x D device reals):
+ *   f_out   T x D device reals: f_t(s_{t-1}) (s_{-1} = s0);
+ *   jac_out device reals: T x D for DIAG/DIAG_HUTCH/ZERO, T x D x D (row-major) for DENSE;
+ *           damping and clip applied (may be NULL);
+ *   acc_out T device bytes: the accept decision of each step (may be NULL);
+ *   ell_out T device doubles: MALA log-ratio / HMC H0 - HL before min(0, .) (may be NULL).
+ */
+pmcmc_status pmcmc_linearize(pmcmc_ctx *ctx, const pmcmc_target *target,
+                             const pmcmc_options *opt, int T, const void *s0, const void *s,
+                             const void *xi, const double *u, void *f_out, void *jac_out,
+                             unsigned char *acc_out, double *ell_out, void *stream);
+
+/*
+ * The parallel affine scan alone (step (b), Section 2): for t = 0..T-1,
+ *   delta_t = a_t (.) delta_{t-1} + b_t  (delta_{-1} = 0),   s_t <- s_t + delta_t.
+ * kind PMCMC_JAC_DIAG: a, b are T x D (elementwise maps, quasi-DEER Eq. 4);
+ * kind PMCMC_JAC_DENSE: a is T x D x D row-major (a_t delta is a matrix-vector product), b T x D.
+ * precision: F64 (a, b, s double), F32 (float), F32_SCAN_BF16 (a, b bfloat16, s float).
+ * s: T x D device, updated in place.  Single pass, decoupled look-back.
+ */
+pmcmc_status pmcmc_scan(pmcmc_ctx *ctx, pmcmc_jac kind, pmcmc_precision precision, int T, int D,
+                        const void *a, const void *b, void *s, void *stream);
+
+/*
+ * Adjoint of a chain functional at the converged fixed point, with every accept decision held
+ * (the chain is then a smooth function of the parameters).  Given dL/ds (T x D device reals)
+ * it runs the transposed recursion backward,
+ *   lambda_t = dL/ds_t + J_{t+1}^T lambda_{t+1},   lambda_T = dL/ds_T,
+ * as a parallel reverse scan with dense J_{t+1} = I + step H(s_t) (accepted) or I (rejected),
+ * and returns dL/dtheta = sum_t lambda_t^T d f_t/d theta for theta = (step, prior_scale).
+ * J is recomputed in segments when T*D*D reals exceed jac_budget_bytes (0 = no limit).
+ * Only PMCMC_MALA.  s: the converged trajectory; acc: its T decisions (device bytes).
+ * grad_out: 2 host doubles.
+ */
+pmcmc_status pmcmc_adjoint(pmcmc_ctx *ctx, const pmcmc_target *target, const pmcmc_options *opt,
+                           int T, const void *s0, const void *s, const unsigned char *acc,
+                           const void *xi, const double *u, const void *dL_ds,
+                           size_t jac_budget_bytes, double *grad_out, void *stream);
+
+/* One chain of a batched solve. */
+typedef struct {
+    pmcmc_target target;
+    pmcmc_sampler sampler; /* PMCMC_MALA or PMCMC_HMC */
+    double step;
+    int leapfrog_L;
+    int T;
+    const void *s0;        /* D device reals */
+    const void *xi;        /* T x D device reals */
+    const double *u;       /* T device doubles */
+    void *s_out;           /* T x D device reals */
+} pmcmc_chain_desc;
+
+/*
+ * Many independent chains of uneven T, D, sampler and target solved together (the batching
+ * of Section 5.2) by one persistent kernel per Newton sweep, captured in a CUDA graph whose
+ * device-side loop runs until every chain has converged.  Uses opt->jac (DIAG or
+ * DIAG_HUTCH), opt->precision (F32 or F32_SCAN_BF16), atol/rtol, max_iters, damping, clip.
+ * Per-chain results go to res (B host structs, may be NULL).
+ */
+pmcmc_status pmcmc_solve_batched(pmcmc_ctx *ctx, int B, const pmcmc_chain_desc *chains,
+                                 const pmcmc_options *opt, pmcmc_result *res, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMCMC_H */

@@ -266,3 +266,13 @@ def gen_noise(seed: int, chain_id: int, T: int, D: int, raw: bool = False):
     if raw:
         return xi, u, w
     return xi, u
+
+
+def linear_recursion(A, b, dense: bool):
+    """delta_t = A_t delta_{t-1} + b_t, delta_{-1} = 0 (the plain loop). Returns delta [T, n]."""
+    A, b = _arr(A), _arr(b)
+    T, n = b.shape
+    out = np.zeros((T, n))
+    _load().o_linear_recursion(C.c_int(T), C.c_int(n), C.c_int(int(dense)), _ptr(A), _ptr(b),
+                               _ptr(out))
+    return out

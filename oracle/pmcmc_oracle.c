@@ -686,3 +686,28 @@ void o_gen_noise(uint64_t seed, uint32_t chain, int T, int D, double *xi, double
         u[t - 1] = u53(w[0], w[1]);
     }
 }
+
+/* ---------------------------------------------------------------------------------------- */
+/* The linear recursion solved by each Newton iteration (Section 2, in delta form)            */
+/* ---------------------------------------------------------------------------------------- */
+
+/*
+ * delta_t = A_t delta_{t-1} + b_t for t = 0..T-1 with delta_{-1} = 0, written out as the plain
+ * sequential loop (the definition the parallel scan must reproduce).
+ * dense = 0: A is T*n (elementwise maps); dense = 1: A is T*n*n row-major.
+ * Pinned by: brute-force sums of products of the maps on tiny inputs.
+ */
+void o_linear_recursion(int T, int n, int dense, const double *A, const double *b, double *delta) {
+    double *prev = dalloc(n), *tmp = dalloc(n);
+    for (int t = 0; t < T; t++) {
+        if (dense)
+            matvec(n, A + (size_t)t * n * n, prev, tmp);
+        else
+            for (int d = 0; d < n; d++) tmp[d] = A[(size_t)t * n + d] * prev[d];
+        for (int d = 0; d < n; d++) {
+            prev[d] = tmp[d] + b[(size_t)t * n + d];
+            delta[(size_t)t * n + d] = prev[d];
+        }
+    }
+    free(prev); free(tmp);
+}

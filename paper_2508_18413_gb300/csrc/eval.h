@@ -1,0 +1,60 @@
+// Arguments of the evaluate-and-linearise kernels (step (a) of a Newton iteration).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/pmcmc.h"
+
+namespace pm {
+
+struct EvalStats;
+
+struct EvalArgs {
+    // problem
+    int target = 0;      // pmcmc_target_kind
+    int sampler = 0;     // pmcmc_sampler
+    int T = 0, D = 0, L = 0, N = 0;
+    double eps = 0.0;
+    double sigma_p = 1.0;
+    int jac = PMCMC_JAC_DIAG;
+    int gate_grad = 1;
+    double damping = 1.0;
+    int clip = 0;
+    double rtol = 0.0;
+    bool f64 = false;    // arithmetic type double (else float)
+    bool bf16 = false;   // scan pair storage bfloat16 (FP32 arithmetic)
+    // inputs (device)
+    const void *s0 = nullptr;   // D
+    const void *s = nullptr;    // T x D current iterate
+    const void *xi = nullptr;   // T x D
+    const double *u = nullptr;  // T
+    const void *mu = nullptr;   // Gaussian mean
+    const void *P = nullptr;    // Gaussian precision
+    const void *X = nullptr;    // logistic design N x D
+    const void *Xp = nullptr;   // logistic design, padded copy (workspace)
+    const void *y = nullptr;    // logistic labels
+    // outputs (device, optional)
+    void *a_out = nullptr;      // J: T x D (diag) or T x D x D (dense)
+    void *b_out = nullptr;      // r = f - s: T x D
+    void *f_out = nullptr;      // f: T x D
+    unsigned char *acc_out = nullptr;
+    double *ell_out = nullptr;
+    void *w_out = nullptr;      // logistic dense J: sigmoid'(z) per (t, n), T x N
+    void *rank1_u = nullptr;    // logistic dense J: gate term vectors, T x D each
+    void *rank1_v = nullptr;
+    EvalStats *stats = nullptr;
+    // probes / control
+    unsigned long long seed = 0;
+    unsigned int chain = 0;
+    const int *iter = nullptr;  // device Newton iteration counter (Hutchinson probes)
+    const int *skip = nullptr;  // device flag: skip the launch when set (device-side loop)
+};
+
+cudaError_t launch_eval_small(const EvalArgs &A, cudaStream_t st);
+cudaError_t launch_seq_small(const EvalArgs &A, cudaStream_t st);
+cudaError_t launch_eval_logreg(const EvalArgs &A, cudaStream_t st);
+cudaError_t launch_seq_logreg(const EvalArgs &A, cudaStream_t st);
+cudaError_t launch_logreg_dense_jac(const EvalArgs &A, cudaStream_t st);
+int logreg_padded_dim(int D);
+
+}  // namespace pm

@@ -1,0 +1,44 @@
+// Internal launch interfaces shared by the translation units of libpmcmc.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+
+#include "../../include/pmcmc.h"
+
+namespace pm {
+
+struct ScanCtl;
+struct EvalStats;
+
+constexpr unsigned int kDefaultSpinLimit = 1u << 22;
+
+// Workspace for one decoupled look-back scan: per-tile flags and aggregates.
+struct ScanWork {
+    unsigned int *flags = nullptr;  // ntiles, zero-initialised once
+    void *agg = nullptr;            // ntiles * (D*D + D) reals (dense) or 2*D (diag)
+    void *incl = nullptr;           // ntiles * D reals
+    int max_tiles = 0;
+    ScanCtl *ctl = nullptr;
+};
+
+// Tile geometry of the diagonal scan for (T, D): timesteps per tile.
+int diag_scan_tile(int T, int D, int elem_bytes);
+int dense_scan_chunk(int T, int D);
+
+cudaError_t launch_noise(unsigned long long seed, unsigned int chain, int T, int D, bool f64,
+                         void *xi, double *u, cudaStream_t st);
+
+// storage: 0 = same as arithmetic, 1 = bfloat16 (FP32 arithmetic only)
+cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, const void *a,
+                             const void *b, void *s, const void *s_reset, const ScanWork &w,
+                             EvalStats *stats, const int *skip, unsigned int spin_limit,
+                             cudaStream_t st);
+
+cudaError_t launch_scan_dense(bool f64, int T, int D, int chunk, const void *a, const void *b,
+                              void *s, const void *s_reset, const ScanWork &w, EvalStats *stats,
+                              const int *skip, unsigned int spin_limit, cudaStream_t st);
+
+}  // namespace pm

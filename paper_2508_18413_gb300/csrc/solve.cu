@@ -1,0 +1,661 @@
+// Host side of libpmcmc: context, workspace, the C ABI of include/pmcmc.h and the Newton loop
+// of Algorithm 1.  Every arithmetic step runs in the kernels; this file only sizes buffers,
+// launches, and reads back the per-iteration statistics.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "eval.h"
+#include "internal.h"
+#include "solve.h"
+
+using namespace pm;
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+static pmcmc_status fail(pmcmc_ctx *c, pmcmc_status st, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+#define PM_CUDA(c, call)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((c), PMCMC_ECUDA, "%s failed: %s (%s:%d)", #call,                    \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+    } while (0)
+
+namespace pm {
+
+pmcmc_status set_error(pmcmc_ctx *c, pmcmc_status st, const char *msg) {
+    return fail(c, st, "%s", msg);
+}
+
+// ------------------------------------------------------------------------------------------
+// workspace
+// ------------------------------------------------------------------------------------------
+pmcmc_status ws_reserve(pmcmc_ctx *c, size_t bytes) {
+    if (bytes <= c->ws_bytes) return PMCMC_OK;
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&c->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PMCMC_ENOMEM, "workspace allocation of %zu bytes failed", bytes);
+        }
+        want = bytes;
+    }
+    c->ws_bytes = want;
+    c->ws_generation++;
+    return PMCMC_OK;
+}
+
+size_t Carve::take(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + bytes;
+    return off;
+}
+
+static void stats_reset_host(EvalStats &s) {
+    s.err = kOrdNegInf;
+    s.rmax = 0x8000000000000000ull;  // +0.0
+    s.min_margin = 0xfff0000000000000ull;  // +inf
+    s.accepts = 0;
+    s.resets = 0;
+    s.dmax = 0x8000000000000000ull;
+}
+
+__global__ void stats_reset_kernel(EvalStats *s, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        s[i].err = kOrdNegInf;
+        s[i].rmax = 0x8000000000000000ull;
+        s[i].min_margin = 0xfff0000000000000ull;
+        s[i].accepts = 0;
+        s[i].resets = 0;
+        s[i].dmax = 0x8000000000000000ull;
+    }
+}
+
+__global__ void broadcast_rows_kernel(void *dst, const void *row, int T, int D, int esz) {
+    size_t n = (size_t)T * D;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int d = (int)(i % D);
+        if (esz == 8)
+            ((double *)dst)[i] = ((const double *)row)[d];
+        else
+            ((float *)dst)[i] = ((const float *)row)[d];
+    }
+}
+
+// Zero-padded copy of the design matrix: Xp[n][k] = X[n][k] for n < N, k < D, else 0.
+__global__ void pad_rows_kernel(void *dst, const void *src, int N, int D, int Npad, int DP,
+                                int esz) {
+    size_t n = (size_t)Npad * DP;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(i / DP), k = (int)(i % DP);
+        bool in = r < N && k < D;
+        if (esz == 8)
+            ((double *)dst)[i] = in ? ((const double *)src)[(size_t)r * D + k] : 0.0;
+        else
+            ((float *)dst)[i] = in ? ((const float *)src)[(size_t)r * D + k] : 0.f;
+    }
+}
+
+// all-finite check of a device array (sets *flag to 1 on a non-finite entry)
+__global__ void finite_check_kernel(const void *p, size_t n, int esz, int *flag) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        double v = esz == 8 ? ((const double *)p)[i] : (double)((const float *)p)[i];
+        if (!isfinite(v)) *flag = 1;
+    }
+}
+
+static int grid_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)std::max<size_t>(1, std::min<size_t>(b, 152 * 8));
+}
+
+}  // namespace pm
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+void pmcmc_options_default(pmcmc_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->sampler = PMCMC_MALA;
+    o->step = 0.01;
+    o->leapfrog_L = 0;
+    o->jac = PMCMC_JAC_DIAG;
+    o->precision = PMCMC_F32;
+    o->atol = 1e-5;
+    o->rtol = 0.0;
+    o->max_iters = 0;
+    o->damping = 1.0;
+    o->clip = 0;
+    o->gate_grad = 1;
+    o->seed = 0;
+    o->chain_id = 0;
+    o->spin_limit = 0;
+}
+
+pmcmc_status pmcmc_create(pmcmc_ctx **out, int device) {
+    if (!out) return PMCMC_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return PMCMC_EINVAL;
+    }
+    pmcmc_ctx *c = new pmcmc_ctx();
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return PMCMC_ECUDA;
+    }
+    if (cudaMalloc(&c->ctl, sizeof(CtlBlock)) != cudaSuccess ||
+        cudaMallocHost(&c->host_ctl, sizeof(CtlBlock)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PMCMC_ENOMEM;
+    }
+    CtlBlock init;
+    memset(&init, 0, sizeof(init));
+    init.scan.epoch = 1;
+    for (int i = 0; i < kMaxStats; i++) stats_reset_host(init.stats[i]);
+    if (cudaMemcpy(c->ctl, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        pmcmc_destroy(c);
+        return PMCMC_ECUDA;
+    }
+    *out = c;
+    return PMCMC_OK;
+}
+
+pmcmc_status pmcmc_destroy(pmcmc_ctx *c) {
+    if (!c) return PMCMC_OK;
+    cudaSetDevice(c->device);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->ws) cudaFree(c->ws);
+    if (c->ctl) cudaFree(c->ctl);
+    if (c->host_ctl) cudaFreeHost(c->host_ctl);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return PMCMC_OK;
+}
+
+const char *pmcmc_last_error(pmcmc_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+pmcmc_status pmcmc_gen_noise(pmcmc_ctx *c, unsigned long long seed, unsigned int chain, int T,
+                             int D, pmcmc_precision prec, void *xi, double *u, void *stream) {
+    if (!c) return PMCMC_EINVAL;
+    if (T < 0 || D < 0 || (T > 0 && D > 0 && !xi && !u))
+        return fail(c, PMCMC_EINVAL, "gen_noise: invalid sizes or no output");
+    if (T == 0) return PMCMC_OK;
+    PM_CUDA(c, cudaSetDevice(c->device));
+    PM_CUDA(c, launch_noise(seed, chain, T, D, prec == PMCMC_F64, D > 0 ? xi : nullptr, u,
+                            (cudaStream_t)stream));
+    return PMCMC_OK;
+}
+
+pmcmc_status pmcmc_scan(pmcmc_ctx *c, pmcmc_jac kind, pmcmc_precision prec, int T, int D,
+                        const void *a, const void *b, void *s, void *stream) {
+    if (!c) return PMCMC_EINVAL;
+    if (T < 0 || D <= 0 || !a || !b || !s) return fail(c, PMCMC_EINVAL, "scan: invalid arguments");
+    if (T == 0) return PMCMC_OK;
+    PM_CUDA(c, cudaSetDevice(c->device));
+    const bool f64 = prec == PMCMC_F64;
+    const int rb = f64 ? 8 : 4;
+    cudaStream_t st = (cudaStream_t)stream;
+    ScanWork w;
+    int tiles;
+    int tile_t = 0;
+    if (kind == PMCMC_JAC_DIAG) {
+        if (D > 256) return fail(c, PMCMC_EUNSUPPORTED, "scan: diagonal scan supports D <= 256");
+        tile_t = diag_scan_tile(T, D, rb);
+        tiles = ceil_div(T, tile_t);
+    } else if (kind == PMCMC_JAC_DENSE) {
+        if (D > 32) return fail(c, PMCMC_EUNSUPPORTED, "scan: dense scan supports D <= 32");
+        if (prec == PMCMC_F32_SCAN_BF16)
+            return fail(c, PMCMC_EUNSUPPORTED, "scan: dense scan has no bfloat16 storage");
+        tile_t = dense_scan_chunk(T, D);
+        tiles = ceil_div(T, tile_t);
+    } else {
+        return fail(c, PMCMC_EINVAL, "scan: kind must be DIAG or DENSE");
+    }
+    Carve cv;
+    size_t o_flags = cv.take(sizeof(unsigned int) * tiles);
+    size_t o_agg = cv.take((size_t)rb * tiles * ((size_t)D * D + 2 * D));
+    size_t o_incl = cv.take((size_t)rb * tiles * D);
+    pmcmc_status ps = ws_reserve(c, cv.used);
+    if (ps != PMCMC_OK) return ps;
+    char *base = (char *)c->ws;
+    w.flags = (unsigned int *)(base + o_flags);
+    w.agg = base + o_agg;
+    w.incl = base + o_incl;
+    w.max_tiles = tiles;
+    w.ctl = &c->ctl->scan;
+    if (c->flags_generation != c->ws_generation || c->flags_zeroed < (size_t)tiles) {
+        PM_CUDA(c, cudaMemsetAsync(w.flags, 0, sizeof(unsigned int) * tiles, st));
+    }
+    // flags of this layout are zero or carry an older epoch from here on
+    c->flags_generation = c->ws_generation;
+    c->flags_zeroed = std::max(c->flags_zeroed, (size_t)tiles);
+    c->flags_offset = o_flags;
+    if (kind == PMCMC_JAC_DIAG)
+        PM_CUDA(c, launch_scan_diag(f64, prec == PMCMC_F32_SCAN_BF16 ? 1 : 0, T, D, tile_t, a, b,
+                                    s, nullptr, w, nullptr, nullptr, kDefaultSpinLimit, st));
+    else
+        PM_CUDA(c, launch_scan_dense(f64, T, D, tile_t, a, b, s, nullptr, w, nullptr, nullptr,
+                                     kDefaultSpinLimit, st));
+    return PMCMC_OK;
+}
+
+}  // extern "C"
+
+// ==========================================================================================
+// Solve plumbing
+// ==========================================================================================
+namespace pm {
+
+pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
+                           const void *s0, bool sequential) {
+    if (!tg || !o || !s0) return fail(c, PMCMC_EINVAL, "null target, options or s0");
+    if (T < 0) return fail(c, PMCMC_EINVAL, "T must be >= 0");
+    const int D = tg->D;
+    if (D <= 0) return fail(c, PMCMC_EINVAL, "D must be > 0");
+    if (!(o->step > 0.0)) return fail(c, PMCMC_EINVAL, "step must be > 0");
+    if (o->sampler != PMCMC_MALA && o->sampler != PMCMC_HMC && o->sampler != PMCMC_HMC_PAR_LEAPFROG)
+        return fail(c, PMCMC_EINVAL, "unknown sampler");
+    if ((o->sampler == PMCMC_HMC || o->sampler == PMCMC_HMC_PAR_LEAPFROG) && o->leapfrog_L < 1)
+        return fail(c, PMCMC_EINVAL, "HMC needs leapfrog_L >= 1");
+    if (o->precision < PMCMC_F64 || o->precision > PMCMC_F32_SCAN_BF16)
+        return fail(c, PMCMC_EINVAL, "unknown precision");
+    if (o->jac < PMCMC_JAC_DENSE || o->jac > PMCMC_JAC_ZERO)
+        return fail(c, PMCMC_EINVAL, "unknown Jacobian kind");
+    switch (tg->kind) {
+    case PMCMC_GAUSSIAN:
+        if (!tg->mean || !tg->prec) return fail(c, PMCMC_EINVAL, "Gaussian needs mean and prec");
+        if (D > 32) return fail(c, PMCMC_EUNSUPPORTED, "Gaussian target supports D <= 32");
+        break;
+    case PMCMC_BANANA:
+        if (D != 2) return fail(c, PMCMC_EINVAL, "banana target has D = 2");
+        break;
+    case PMCMC_LOGREG:
+        if (!tg->X || !tg->y || tg->N <= 0) return fail(c, PMCMC_EINVAL, "logreg needs X, y, N > 0");
+        if (!(tg->prior_scale > 0.0)) return fail(c, PMCMC_EINVAL, "prior_scale must be > 0");
+        if (logreg_padded_dim(D) < 0) return fail(c, PMCMC_EUNSUPPORTED, "logreg supports D <= 128");
+        if (o->precision == PMCMC_F64 && D > 64)
+            return fail(c, PMCMC_EUNSUPPORTED, "logreg in FP64 supports D <= 64");
+        break;
+    default:
+        return fail(c, PMCMC_EINVAL, "unknown target kind");
+    }
+    if (o->jac == PMCMC_JAC_BLOCK2 && o->sampler != PMCMC_HMC_PAR_LEAPFROG)
+        return fail(c, PMCMC_EINVAL, "BLOCK2 Jacobian is for PMCMC_HMC_PAR_LEAPFROG");
+    if (o->jac == PMCMC_JAC_DENSE) {
+        if (D > 32) return fail(c, PMCMC_EUNSUPPORTED, "dense Newton supports D <= 32");
+        if (o->precision == PMCMC_F32_SCAN_BF16)
+            return fail(c, PMCMC_EUNSUPPORTED, "dense Newton has no bfloat16 scan");
+        if (tg->kind == PMCMC_LOGREG && o->sampler != PMCMC_MALA)
+            return fail(c, PMCMC_EUNSUPPORTED, "dense logreg Jacobian is for MALA");
+    }
+    if (tg->kind == PMCMC_LOGREG && o->sampler != PMCMC_MALA && !sequential)
+        return fail(c, PMCMC_EUNSUPPORTED, "logreg Newton solves support MALA");
+    return PMCMC_OK;
+}
+
+void fill_eval_args(EvalArgs &A, const pmcmc_target *tg, const pmcmc_options *o, int T) {
+    A.target = tg->kind;
+    A.sampler = o->sampler;
+    A.T = T;
+    A.D = tg->D;
+    A.L = o->leapfrog_L;
+    A.N = tg->N;
+    A.eps = o->step;
+    A.sigma_p = tg->prior_scale > 0 ? tg->prior_scale : 1.0;
+    A.jac = o->jac;
+    A.gate_grad = o->gate_grad;
+    A.damping = o->damping > 0 ? o->damping : 1.0;
+    A.clip = o->clip;
+    A.rtol = o->rtol;
+    A.f64 = o->precision == PMCMC_F64;
+    A.bf16 = o->precision == PMCMC_F32_SCAN_BF16;
+    A.mu = tg->mean;
+    A.P = tg->prec;
+    A.X = tg->X;
+    A.y = tg->y;
+    A.seed = o->seed;
+    A.chain = o->chain_id;
+}
+
+// Workspace plan for one solve.
+struct Plan {
+    size_t o_a = 0, o_b = 0, o_xi = 0, o_u = 0, o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0;
+    size_t o_flags = 0, o_agg = 0, o_incl = 0, o_tmp = 0;
+    int tiles = 0, tile_t = 0;
+    size_t bytes = 0;
+};
+
+static Plan make_plan(const pmcmc_target *tg, const pmcmc_options *o, int T, bool gen_noise,
+                      bool need_tmp) {
+    Plan p;
+    Carve cv;
+    const int D = tg->D;
+    const bool f64 = o->precision == PMCMC_F64;
+    const int rb = f64 ? 8 : 4;
+    const int sb = o->precision == PMCMC_F32_SCAN_BF16 ? 2 : rb;
+    const bool dense = o->jac == PMCMC_JAC_DENSE;
+    p.o_a = cv.take(dense ? (size_t)rb * T * D * D : (size_t)sb * T * D);
+    p.o_b = cv.take((size_t)sb * T * D);
+    if (gen_noise) {
+        p.o_xi = cv.take((size_t)rb * T * D);
+        p.o_u = cv.take(sizeof(double) * (size_t)T);
+    }
+    if (tg->kind == PMCMC_LOGREG) {
+        const int DP = logreg_padded_dim(D);
+        const int Npad = ceil_div(tg->N, 64) * 64;
+        p.o_xp = cv.take((size_t)rb * Npad * DP);
+        if (dense) {
+            p.o_w = cv.take((size_t)rb * T * tg->N);
+            p.o_ru = cv.take((size_t)rb * T * D);
+            p.o_rv = cv.take((size_t)rb * T * D);
+        }
+    }
+    p.o_acc = cv.take((size_t)T);
+    if (dense) {
+        p.tile_t = dense_scan_chunk(T, D);
+    } else {
+        p.tile_t = diag_scan_tile(T, D, rb);
+    }
+    p.tiles = std::max(1, ceil_div(T, p.tile_t));
+    p.o_flags = cv.take(sizeof(unsigned int) * p.tiles);
+    p.o_agg = cv.take((size_t)rb * p.tiles * ((size_t)D * D + 2 * D));
+    p.o_incl = cv.take((size_t)rb * p.tiles * D);
+    if (need_tmp) p.o_tmp = cv.take((size_t)rb * T * D);
+    p.bytes = cv.used;
+    return p;
+}
+
+}  // namespace pm
+
+extern "C" pmcmc_status pmcmc_solve(pmcmc_ctx *c, const pmcmc_target *tg,
+                                    const pmcmc_options *o, int T, const void *s0,
+                                    const void *s_init, const void *xi, const double *u,
+                                    void *s_out, pmcmc_result *res, void *stream) {
+    if (!c) return PMCMC_EINVAL;
+    if (res) memset(res, 0, sizeof(*res));
+    pmcmc_status ps = check_problem(c, tg, o, T, s0, false);
+    if (ps != PMCMC_OK) return ps;
+    if (T > 0 && !s_out) return fail(c, PMCMC_EINVAL, "s_out is NULL");
+    if ((xi == nullptr) != (u == nullptr)) return fail(c, PMCMC_EINVAL, "pass both xi and u, or neither");
+    if (T == 0) {
+        if (res) res->status = PMCMC_OK;
+        return PMCMC_OK;
+    }
+    PM_CUDA(c, cudaSetDevice(c->device));
+    if (o->sampler == PMCMC_HMC_PAR_LEAPFROG)
+        return solve_par_leapfrog(c, tg, o, T, s0, xi, u, s_out, res, stream);
+    return newton_solve(c, tg, o, T, s0, s_init, xi, u, s_out, res, stream);
+}
+
+namespace pm {
+
+pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
+                          const void *s0, const void *s_init, const void *xi, const double *u,
+                          void *s_out, pmcmc_result *res, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = tg->D;
+    const bool f64 = o->precision == PMCMC_F64;
+    const int rb = f64 ? 8 : 4;
+    const bool gen = xi == nullptr;
+    Plan p = make_plan(tg, o, T, gen, false);
+    pmcmc_status ps = ws_reserve(c, p.bytes);
+    if (ps != PMCMC_OK) return ps;
+    char *base = (char *)c->ws;
+    ScanWork w;
+    w.flags = (unsigned int *)(base + p.o_flags);
+    w.agg = base + p.o_agg;
+    w.incl = base + p.o_incl;
+    w.max_tiles = p.tiles;
+    w.ctl = &c->ctl->scan;
+    if (c->flags_generation != c->ws_generation || c->flags_offset != p.o_flags ||
+        c->flags_zeroed < (size_t)p.tiles) {
+        PM_CUDA(c, cudaMemsetAsync(w.flags, 0, sizeof(unsigned int) * p.tiles, st));
+        c->flags_generation = c->ws_generation;
+        c->flags_offset = p.o_flags;
+        c->flags_zeroed = p.tiles;
+    }
+    // inputs
+    if (gen) {
+        xi = base + p.o_xi;
+        u = (const double *)(base + p.o_u);
+        PM_CUDA(c, launch_noise(o->seed, o->chain_id, T, D, f64, (void *)xi, (double *)u, st));
+    }
+    if (tg->kind == PMCMC_LOGREG) {
+        const int DP = logreg_padded_dim(D);
+        const int Npad = ceil_div(tg->N, 64) * 64;
+        pad_rows_kernel<<<grid_for((size_t)Npad * DP), 256, 0, st>>>(base + p.o_xp, tg->X, tg->N,
+                                                                     D, Npad, DP, rb);
+        PM_CUDA(c, cudaGetLastError());
+    }
+    // initial guess: s^(0) = s_init, or s0 broadcast (Appendix B)
+    if (s_init) {
+        if (s_init != s_out)
+            PM_CUDA(c, cudaMemcpyAsync(s_out, s_init, (size_t)rb * T * D, cudaMemcpyDeviceToDevice, st));
+    } else {
+        broadcast_rows_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(s_out, s0, T, D, rb);
+        PM_CUDA(c, cudaGetLastError());
+    }
+    // finite check of s0 / the initial guess
+    {
+        int *flag = &c->ctl->nonfinite_input;
+        PM_CUDA(c, cudaMemsetAsync(flag, 0, sizeof(int), st));
+        finite_check_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(s_out, (size_t)T * D, rb, flag);
+        finite_check_kernel<<<1, 256, 0, st>>>(s0, (size_t)D, rb, flag);
+        PM_CUDA(c, cudaGetLastError());
+    }
+
+    EvalArgs A;
+    fill_eval_args(A, tg, o, T);
+    A.s0 = s0;
+    A.s = s_out;
+    A.xi = xi;
+    A.u = u;
+    A.Xp = base + p.o_xp;
+    A.a_out = base + p.o_a;
+    A.b_out = base + p.o_b;
+    A.acc_out = (unsigned char *)(base + p.o_acc);
+    if (tg->kind == PMCMC_LOGREG && o->jac == PMCMC_JAC_DENSE) {
+        A.w_out = base + p.o_w;
+        A.rank1_u = base + p.o_ru;
+        A.rank1_v = base + p.o_rv;
+    }
+    EvalStats *stats = &c->ctl->stats[0];
+    A.stats = stats;
+    A.iter = &c->ctl->iter;
+    const int max_iters = o->max_iters > 0 ? o->max_iters : T;
+    const unsigned int spin = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
+    const double atol = o->atol;
+
+    PM_CUDA(c, cudaEventRecord(c->ev0, st));
+    int it = 0;
+    bool converged = false;
+    CtlBlock *h = c->host_ctl;
+    for (;;) {
+        PM_CUDA(c, cudaMemcpyAsync(&c->ctl->iter, &it, sizeof(int), cudaMemcpyHostToDevice, st));
+        stats_reset_kernel<<<1, 32, 0, st>>>(stats, 1);
+        if (tg->kind == PMCMC_LOGREG) {
+            PM_CUDA(c, launch_eval_logreg(A, st));
+            if (o->jac == PMCMC_JAC_DENSE) PM_CUDA(c, launch_logreg_dense_jac(A, st));
+        } else {
+            PM_CUDA(c, launch_eval_small(A, st));
+        }
+        PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(c, cudaStreamSynchronize(st));
+        if (h->nonfinite_input) return fail(c, PMCMC_ENAN, "s0 or the initial guess is not finite");
+        const double err = ord_decode(h->stats[0].err);
+        if (err <= atol) {
+            converged = true;
+            break;
+        }
+        if (it >= max_iters) break;
+        if (o->jac == PMCMC_JAC_DENSE)
+            PM_CUDA(c, launch_scan_dense(f64, T, D, p.tile_t, A.a_out, A.b_out, s_out, s0, w, stats,
+                                         nullptr, spin, st));
+        else
+            PM_CUDA(c, launch_scan_diag(f64, A.bf16 ? 1 : 0, T, D, p.tile_t, A.a_out, A.b_out, s_out,
+                                        s0, w, stats, nullptr, spin, st));
+        it++;
+        c->resets_accum += 0;  // counted from the stats below
+        PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(c, cudaStreamSynchronize(st));
+        c->resets_accum += h->stats[0].resets;
+        if (h->scan.timeout) break;
+    }
+    PM_CUDA(c, cudaEventRecord(c->ev1, st));
+    PM_CUDA(c, cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    pmcmc_status status = converged ? PMCMC_OK : PMCMC_NOT_CONVERGED;
+    if (h->scan.timeout) {
+        unsigned int zero = 0;
+        cudaMemcpy(&c->ctl->scan.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        status = PMCMC_ETIMEOUT;
+        fail(c, status, "a look-back wait in the scan ran out");
+    }
+    if (res) {
+        res->iters = it;
+        res->status = status;
+        res->max_residual = ord_decode(h->stats[0].rmax);
+        res->accept_rate = (double)h->stats[0].accepts / (double)T;
+        res->min_margin = ord_decode(h->stats[0].min_margin);
+        res->nonfinite_resets = (int)c->resets_accum;
+        res->elapsed_ms = ms;
+    }
+    c->resets_accum = 0;
+    return status;
+}
+
+}  // namespace pm
+
+extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
+                                        const pmcmc_options *o, int T, const void *s0,
+                                        const void *s, const void *xi, const double *u,
+                                        void *f_out, void *jac_out, unsigned char *acc_out,
+                                        double *ell_out, void *stream) {
+    if (!c) return PMCMC_EINVAL;
+    pmcmc_status ps = check_problem(c, tg, o, T, s0, false);
+    if (ps != PMCMC_OK) return ps;
+    if (o->sampler == PMCMC_HMC_PAR_LEAPFROG)
+        return fail(c, PMCMC_EINVAL, "linearize: use MALA or HMC");
+    if (!s || !xi || !u) return fail(c, PMCMC_EINVAL, "linearize needs s, xi and u");
+    if (o->precision == PMCMC_F32_SCAN_BF16)
+        return fail(c, PMCMC_EINVAL, "linearize: use F32 or F64");
+    if (T == 0) return PMCMC_OK;
+    PM_CUDA(c, cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = tg->D;
+    const bool f64 = o->precision == PMCMC_F64;
+    const int rb = f64 ? 8 : 4;
+    Carve cv;
+    size_t o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0, o_j = 0;
+    const bool dense = o->jac == PMCMC_JAC_DENSE;
+    if (tg->kind == PMCMC_LOGREG) {
+        const int DP = logreg_padded_dim(D);
+        o_xp = cv.take((size_t)rb * ceil_div(tg->N, 64) * 64 * DP);
+        if (dense) {
+            o_w = cv.take((size_t)rb * T * tg->N);
+            o_ru = cv.take((size_t)rb * T * D);
+            o_rv = cv.take((size_t)rb * T * D);
+            o_acc = cv.take((size_t)T);
+        }
+    }
+    if (dense && !jac_out) o_j = cv.take((size_t)rb * T * D * D);
+    ps = ws_reserve(c, std::max<size_t>(cv.used, 256));
+    if (ps != PMCMC_OK) return ps;
+    char *base = (char *)c->ws;
+    EvalArgs A;
+    fill_eval_args(A, tg, o, T);
+    A.s0 = s0;
+    A.s = s;
+    A.xi = xi;
+    A.u = u;
+    A.f_out = f_out;
+    A.a_out = jac_out ? jac_out : (dense ? (void *)(base + o_j) : nullptr);
+    A.acc_out = acc_out;
+    A.ell_out = ell_out;
+    A.iter = &c->ctl->iter;
+    if (tg->kind == PMCMC_LOGREG) {
+        const int DP = logreg_padded_dim(D);
+        const int Npad = ceil_div(tg->N, 64) * 64;
+        A.Xp = base + o_xp;
+        pad_rows_kernel<<<grid_for((size_t)Npad * DP), 256, 0, st>>>(base + o_xp, tg->X, tg->N, D,
+                                                                     Npad, DP, rb);
+        if (dense) {
+            A.w_out = base + o_w;
+            A.rank1_u = base + o_ru;
+            A.rank1_v = base + o_rv;
+            if (!acc_out) A.acc_out = (unsigned char *)(base + o_acc);
+        }
+        PM_CUDA(c, launch_eval_logreg(A, st));
+        if (dense) PM_CUDA(c, launch_logreg_dense_jac(A, st));
+    } else {
+        PM_CUDA(c, launch_eval_small(A, st));
+    }
+    PM_CUDA(c, cudaStreamSynchronize(st));
+    return PMCMC_OK;
+}
+
+extern "C" pmcmc_status pmcmc_seq_solve(pmcmc_ctx *c, const pmcmc_target *tg,
+                                        const pmcmc_options *o, int T, const void *s0,
+                                        const void *xi, const double *u, void *s_out,
+                                        unsigned char *accept_out, void *stream) {
+    if (!c) return PMCMC_EINVAL;
+    pmcmc_status ps = check_problem(c, tg, o, T, s0, true);
+    if (ps != PMCMC_OK) return ps;
+    if (!s_out || !xi || !u) return fail(c, PMCMC_EINVAL, "seq_solve needs xi, u and s_out");
+    if (o->precision == PMCMC_F32_SCAN_BF16) return fail(c, PMCMC_EINVAL, "seq_solve: F32 or F64");
+    if (T == 0) return PMCMC_OK;
+    PM_CUDA(c, cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    pmcmc_options oo = *o;
+    if (oo.sampler == PMCMC_HMC_PAR_LEAPFROG) oo.sampler = PMCMC_HMC;
+    EvalArgs A;
+    fill_eval_args(A, tg, &oo, T);
+    A.s0 = s0;
+    A.xi = xi;
+    A.u = u;
+    A.f_out = s_out;
+    A.acc_out = accept_out;
+    if (tg->kind == PMCMC_LOGREG) {
+        if (tg->N > 20000) return fail(c, PMCMC_EUNSUPPORTED, "seq_solve logreg supports N <= 20000");
+        PM_CUDA(c, launch_seq_logreg(A, st));
+    } else {
+        PM_CUDA(c, launch_seq_small(A, st));
+    }
+    return PMCMC_OK;
+}

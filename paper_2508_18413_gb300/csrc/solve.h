@@ -1,0 +1,68 @@
+// Host-side state shared by the translation units of libpmcmc.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "common.cuh"
+#include "eval.h"
+#include "internal.h"
+
+namespace pm {
+
+constexpr int kMaxStats = 4;
+
+// Device control block of a context (one per context, never reallocated).
+struct CtlBlock {
+    ScanCtl scan;
+    EvalStats stats[kMaxStats];
+    int iter;             // Newton iteration index (read by the Hutchinson probes)
+    int nonfinite_input;  // set when s0 or the initial guess is not finite
+    int converged;
+    int skip;             // device-side loop: set once the loop is finished
+    int iters_done;
+    int pad[3];
+    unsigned long long inner_iters;  // parallel leapfrog: inner Newton iterations, all steps
+    unsigned long long inner_max;
+};
+
+// Bump allocator over the context workspace (offsets, 256-byte aligned).
+struct Carve {
+    size_t used = 0;
+    size_t take(size_t bytes);
+};
+
+}  // namespace pm
+
+struct pmcmc_ctx {
+    int device = 0;
+    std::string err;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned long long ws_generation = 0;
+    pm::CtlBlock *ctl = nullptr;       // device
+    pm::CtlBlock *host_ctl = nullptr;  // pinned host mirror
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned long long flags_generation = ~0ull;
+    size_t flags_offset = 0, flags_zeroed = 0;
+    unsigned long long resets_accum = 0;
+};
+
+namespace pm {
+
+pmcmc_status ws_reserve(pmcmc_ctx *c, size_t bytes);
+pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
+                           const void *s0, bool sequential);
+void fill_eval_args(EvalArgs &A, const pmcmc_target *tg, const pmcmc_options *o, int T);
+pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
+                          const void *s0, const void *s_init, const void *xi, const double *u,
+                          void *s_out, pmcmc_result *res, void *stream);
+pmcmc_status solve_par_leapfrog(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o,
+                                int T, const void *s0, const void *xi, const double *u,
+                                void *s_out, pmcmc_result *res, void *stream);
+pmcmc_status set_error(pmcmc_ctx *c, pmcmc_status st, const char *msg);
+
+}  // namespace pm

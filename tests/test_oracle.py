@@ -519,3 +519,21 @@ def test_non_finite_proposal_rejects_and_deer_does_not_stop_on_nan():
     assert conv and iters <= T and not np.isnan(s).any()
     assert np.isinf(hist).any()
     np.testing.assert_allclose(s, ref, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_linear_recursion_is_sum_of_products(dense):
+    """delta_t = sum_{k<=t} (A_t ... A_{k+1}) b_k, evaluated by explicit products."""
+    rng = np.random.default_rng(3)
+    T, n = 7, 3
+    A = rng.standard_normal((T, n, n) if dense else (T, n))
+    b = rng.standard_normal((T, n))
+    got = O.linear_recursion(A, b, dense)
+    for t in range(T):
+        ref = np.zeros(n)
+        for k in range(t + 1):
+            M = np.eye(n)
+            for j in range(k + 1, t + 1):
+                M = (A[j] if dense else np.diag(A[j])) @ M
+            ref += M @ b[k]
+        np.testing.assert_allclose(got[t], ref, rtol=1e-12, atol=1e-12)
