@@ -231,6 +231,26 @@ typedef struct {
 pmcmc_status pmcmc_solve_batched(pmcmc_ctx *ctx, int B, const pmcmc_chain_desc *chains,
                                  const pmcmc_options *opt, pmcmc_result *res, void *stream);
 
+/*
+ * Measurement support (the paper reports post-compilation wall-clock only, Section 5 and
+ * Appendix B; these counters explain such a number).  While enabled, the context counts every
+ * kernel it launches and brackets each evaluate-and-linearise, dense-Jacobian and scan launch
+ * with CUDA events on the launching stream, accumulating their device durations.
+ * pmcmc_profile_enable(ctx, 1) resets the counters; (ctx, 0) stops recording.
+ */
+typedef struct {
+    long long launches;       /* kernels launched by this context while enabled */
+    long long eval_launches;  /* evaluate-and-linearise launches */
+    double eval_ms;           /* their summed device time */
+    long long jac_launches;   /* dense Jacobian assembly launches */
+    double jac_ms;
+    long long scan_launches;  /* scan launches */
+    double scan_ms;
+} pmcmc_profile;
+
+pmcmc_status pmcmc_profile_enable(pmcmc_ctx *ctx, int enable);
+pmcmc_status pmcmc_profile_get(pmcmc_ctx *ctx, pmcmc_profile *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,8 @@ from ._lib import JACS, PRECISIONS, SAMPLERS, STATUS_NAMES, TARGETS
 __all__ = [
     "PmcmcError", "Target", "Options", "pmcmc_create", "pmcmc_gen_noise", "pmcmc_solve",
     "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan", "pmcmc_adjoint", "pmcmc_solve_batched",
-    "ChainDesc", "real_dtype", "loaded_library_path",
+    "ChainDesc", "real_dtype", "loaded_library_path", "pmcmc_profile_enable",
+    "pmcmc_profile_get",
 ]
 
 
@@ -261,3 +262,16 @@ def pmcmc_solve_batched(chains: list[ChainDesc], opt: Options):
     st = L.load().pmcmc_solve_batched(ctx, len(chains), arr, C.byref(oc), res, _stream())
     _check(ctx, st)
     return [_result_dict(r) for r in res]
+
+
+def pmcmc_profile_enable(enable: bool = True):
+    """Start (and reset) or stop the context's launch counters and kernel event timers."""
+    ctx = pmcmc_create()
+    _check(ctx, L.load().pmcmc_profile_enable(ctx, int(enable)))
+
+
+def pmcmc_profile_get() -> dict:
+    ctx = pmcmc_create()
+    p = L.pmcmc_profile()
+    _check(ctx, L.load().pmcmc_profile_get(ctx, C.byref(p)))
+    return {k: getattr(p, k) for k, _ in L.pmcmc_profile._fields_}

@@ -45,10 +45,16 @@ class pmcmc_chain_desc(C.Structure):
                 ("xi", C.c_void_p), ("u", C.c_void_p), ("s_out", C.c_void_p)]
 
 
+class pmcmc_profile(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("eval_launches", C.c_longlong),
+                ("eval_ms", C.c_double), ("jac_launches", C.c_longlong), ("jac_ms", C.c_double),
+                ("scan_launches", C.c_longlong), ("scan_ms", C.c_double)]
+
+
 EXPORTS = [
     "pmcmc_options_default", "pmcmc_create", "pmcmc_destroy", "pmcmc_last_error",
     "pmcmc_gen_noise", "pmcmc_solve", "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan",
-    "pmcmc_adjoint", "pmcmc_solve_batched",
+    "pmcmc_adjoint", "pmcmc_solve_batched", "pmcmc_profile_enable", "pmcmc_profile_get",
 ]
 
 _lib = None
@@ -92,5 +98,9 @@ def load(path: str = LIB_PATH):
     lib.pmcmc_solve_batched.argtypes = [vp, i, C.POINTER(pmcmc_chain_desc),
                                         C.POINTER(pmcmc_options), C.POINTER(pmcmc_result), vp]
     lib.pmcmc_solve_batched.restype = st
+    lib.pmcmc_profile_enable.argtypes = [vp, i]
+    lib.pmcmc_profile_enable.restype = st
+    lib.pmcmc_profile_get.argtypes = [vp, C.POINTER(pmcmc_profile)]
+    lib.pmcmc_profile_get.restype = st
     _lib = lib
     return lib

@@ -79,10 +79,10 @@ __device__ void xpass(Smem<R, DP> &S, const R *__restrict__ Xp, const R *__restr
     using G = Geo<DP>;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     R acc[G::MT][G::DJ], accw[G::MT][G::DJ];
-    float llp[G::MT];
+    double llp[G::MT];  // FP64 sum over chunks of per-chunk partials (NC/16 terms each)
 #pragma unroll
     for (int i = 0; i < G::MT; i++) {
-        llp[i] = 0.f;
+        llp[i] = 0.0;
 #pragma unroll
         for (int j = 0; j < G::DJ; j++) acc[i][j] = accw[i][j] = R(0);
     }
@@ -124,6 +124,7 @@ __device__ void xpass(Smem<R, DP> &S, const R *__restrict__ Xp, const R *__restr
 #pragma unroll
         for (int i = 0; i < G::MT; i++) {
             const int tl = ty + 16 * i;
+            R llc = R(0);
 #pragma unroll
             for (int j = 0; j < G::NJ; j++) {
                 const int nl = tx + 16 * j;
@@ -134,12 +135,13 @@ __device__ void xpass(Smem<R, DP> &S, const R *__restrict__ Xp, const R *__restr
                 if (MODE == kGrad) {
                     S.Cs[tl * kNC + nl] = valid ? S.ys[nl] - p : R(0);
                     if (want_w) S.Ws[tl * kNC + nl] = valid ? w : R(0);
-                    if (want_ll && valid) llp[i] += (float)(S.ys[nl] * z - softplus(z));
+                    if (want_ll && valid) llc += S.ys[nl] * z - softplus(z);
                     if (wout && valid && t0 + tl < T) wout[(size_t)(t0 + tl) * N + n0 + nl] = w;
                 } else {
                     S.Cs[tl * kNC + nl] = valid ? w * z2[i][j] : R(0);
                 }
             }
+            if (MODE == kGrad && want_ll) llp[i] += (double)llc;
         }
         __syncthreads();
         // G += C X  (and diag(X^T W X) += W X^2)
@@ -172,7 +174,7 @@ __device__ void xpass(Smem<R, DP> &S, const R *__restrict__ Xp, const R *__restr
             if (MODE == kGrad && want_w) S.dh[tl * DP + tx + 16 * j] = accw[i][j];
         }
         if (MODE == kGrad && want_ll) {
-            double l = (double)llp[i];
+            double l = llp[i];
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
             if (tx == 0) S.ll[tl] += l;

@@ -203,11 +203,29 @@ pmcmc_status pmcmc_destroy(pmcmc_ctx *c) {
     if (c->host_ctl) cudaFreeHost(c->host_ctl);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (int i = 0; i < 6; i++)
+        if (c->pev[i]) cudaEventDestroy(c->pev[i]);
     delete c;
     return PMCMC_OK;
 }
 
 const char *pmcmc_last_error(pmcmc_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+pmcmc_status pmcmc_profile_enable(pmcmc_ctx *c, int enable) {
+    if (!c) return PMCMC_EINVAL;
+    PM_CUDA(c, cudaSetDevice(c->device));
+    if (enable && !c->pev[0])
+        for (int i = 0; i < 6; i++) PM_CUDA(c, cudaEventCreate(&c->pev[i]));
+    c->prof_on = enable ? 1 : 0;
+    if (enable) memset(&c->prof, 0, sizeof(c->prof));
+    return PMCMC_OK;
+}
+
+pmcmc_status pmcmc_profile_get(pmcmc_ctx *c, pmcmc_profile *out) {
+    if (!c || !out) return PMCMC_EINVAL;
+    *out = c->prof;
+    return PMCMC_OK;
+}
 
 pmcmc_status pmcmc_gen_noise(pmcmc_ctx *c, unsigned long long seed, unsigned int chain, int T,
                              int D, pmcmc_precision prec, void *xi, double *u, void *stream) {
@@ -454,6 +472,7 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         xi = base + p.o_xi;
         u = (const double *)(base + p.o_u);
         PM_CUDA(c, launch_noise(o->seed, o->chain_id, T, D, f64, (void *)xi, (double *)u, st));
+        prof_count(c);
     }
     if (tg->kind == PMCMC_LOGREG) {
         const int DP = logreg_padded_dim(D);
@@ -461,6 +480,7 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         pad_rows_kernel<<<grid_for((size_t)Npad * DP), 256, 0, st>>>(base + p.o_xp, tg->X, tg->N,
                                                                      D, Npad, DP, rb);
         PM_CUDA(c, cudaGetLastError());
+        prof_count(c);
     }
     // initial guess: s^(0) = s_init, or s0 broadcast (Appendix B)
     if (s_init) {
@@ -469,6 +489,7 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     } else {
         broadcast_rows_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(s_out, s0, T, D, rb);
         PM_CUDA(c, cudaGetLastError());
+        prof_count(c);
     }
     // finite check of s0 / the initial guess
     {
@@ -477,6 +498,7 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         finite_check_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(s_out, (size_t)T * D, rb, flag);
         finite_check_kernel<<<1, 256, 0, st>>>(s0, (size_t)D, rb, flag);
         PM_CUDA(c, cudaGetLastError());
+        prof_count(c, 2);
     }
 
     EvalArgs A;
@@ -508,14 +530,27 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     for (;;) {
         PM_CUDA(c, cudaMemcpyAsync(&c->ctl->iter, &it, sizeof(int), cudaMemcpyHostToDevice, st));
         stats_reset_kernel<<<1, 32, 0, st>>>(stats, 1);
+        prof_count(c);
+        prof_begin(c, 0, st);
         if (tg->kind == PMCMC_LOGREG) {
             PM_CUDA(c, launch_eval_logreg(A, st));
-            if (o->jac == PMCMC_JAC_DENSE) PM_CUDA(c, launch_logreg_dense_jac(A, st));
+            prof_end(c, 0, st);
+            prof_count(c);
+            if (o->jac == PMCMC_JAC_DENSE) {
+                prof_begin(c, 1, st);
+                PM_CUDA(c, launch_logreg_dense_jac(A, st));
+                prof_end(c, 1, st);
+                prof_count(c);
+            }
         } else {
             PM_CUDA(c, launch_eval_small(A, st));
+            prof_end(c, 0, st);
+            prof_count(c);
         }
         PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
         PM_CUDA(c, cudaStreamSynchronize(st));
+        prof_collect(c, 0);
+        if (tg->kind == PMCMC_LOGREG && o->jac == PMCMC_JAC_DENSE) prof_collect(c, 1);
         if (h->nonfinite_input) return fail(c, PMCMC_ENAN, "s0 or the initial guess is not finite");
         const double err = ord_decode(h->stats[0].err);
         if (err <= atol) {
@@ -523,16 +558,19 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
             break;
         }
         if (it >= max_iters) break;
+        prof_begin(c, 2, st);
         if (o->jac == PMCMC_JAC_DENSE)
             PM_CUDA(c, launch_scan_dense(f64, T, D, p.tile_t, A.a_out, A.b_out, s_out, s0, w, stats,
                                          nullptr, spin, st));
         else
             PM_CUDA(c, launch_scan_diag(f64, A.bf16 ? 1 : 0, T, D, p.tile_t, A.a_out, A.b_out, s_out,
                                         s0, w, stats, nullptr, spin, st));
+        prof_end(c, 2, st);
+        prof_count(c);
         it++;
-        c->resets_accum += 0;  // counted from the stats below
         PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
         PM_CUDA(c, cudaStreamSynchronize(st));
+        prof_collect(c, 2);
         c->resets_accum += h->stats[0].resets;
         if (h->scan.timeout) break;
     }

@@ -49,6 +49,10 @@ struct pmcmc_ctx {
     unsigned long long flags_generation = ~0ull;
     size_t flags_offset = 0, flags_zeroed = 0;
     unsigned long long resets_accum = 0;
+    // measurement (pmcmc_profile_*)
+    int prof_on = 0;
+    pmcmc_profile prof{};
+    cudaEvent_t pev[6] = {};
 };
 
 namespace pm {
@@ -64,5 +68,28 @@ pmcmc_status solve_par_leapfrog(pmcmc_ctx *c, const pmcmc_target *tg, const pmcm
                                 int T, const void *s0, const void *xi, const double *u,
                                 void *s_out, pmcmc_result *res, void *stream);
 pmcmc_status set_error(pmcmc_ctx *c, pmcmc_status st, const char *msg);
+
+// Profiling helpers: count a launch; bracket a timed launch (slot 0 eval, 1 jac, 2 scan).
+inline void prof_count(pmcmc_ctx *c, int n = 1) {
+    if (c->prof_on) c->prof.launches += n;
+}
+inline void prof_begin(pmcmc_ctx *c, int slot, cudaStream_t st) {
+    if (c->prof_on) cudaEventRecord(c->pev[2 * slot], st);
+}
+inline void prof_end(pmcmc_ctx *c, int slot, cudaStream_t st) {
+    if (c->prof_on) cudaEventRecord(c->pev[2 * slot + 1], st);
+}
+// after a stream sync: accumulate the durations of the bracketed launches
+inline void prof_collect(pmcmc_ctx *c, int slot) {
+    if (!c->prof_on) return;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->pev[2 * slot], c->pev[2 * slot + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (slot == 0) { c->prof.eval_ms += ms; c->prof.eval_launches++; }
+    if (slot == 1) { c->prof.jac_ms += ms; c->prof.jac_launches++; }
+    if (slot == 2) { c->prof.scan_ms += ms; c->prof.scan_launches++; }
+}
 
 }  // namespace pm
