@@ -208,6 +208,24 @@ pmcmc_status pmcmc_adjoint(pmcmc_ctx *ctx, const pmcmc_target *target, const pmc
                            const void *xi, const double *u, const void *dL_ds,
                            size_t jac_budget_bytes, double *grad_out, void *stream);
 
+/*
+ * The diagonal scan of pmcmc_scan (kind PMCMC_JAC_DIAG) without any allocation and without a
+ * context.  The paper has no counterpart: this exists for callers that cannot allocate device
+ * memory, such as code running during CUDA stream capture (cudaMalloc is not a stream
+ * operation), hosts that fix their memory budget at start-up, and plugins inside a framework
+ * whose allocator owns the device.  Its scratch (look-back flags, tile aggregates, control
+ * words) is one static device array of 8 MiB that every GPU loading the library holds until
+ * process exit.  The first call on a device (with it current) looks up the array's address;
+ * make that call before any stream capture.  Each call clears what must start at zero with
+ * cudaMemsetAsync on `stream`; it neither allocates nor frees.  All calls share the array:
+ * calls that overlap on the GPU race, so order them on one stream.  The call is asynchronous
+ * and does not report device-side look-back timeouts.
+ * Returns EINVAL for bad arguments and EUNSUPPORTED when D > 256 or the scan's scratch
+ * (about 4 + 3 D r bytes per tile of ~4096/D timesteps, r = 4 or 8) exceeds 8 MiB.
+ */
+pmcmc_status pmcmc_scan_noalloc(pmcmc_precision precision, int T, int D, const void *a,
+                                const void *b, void *s, void *stream);
+
 /* One chain of a batched solve. */
 typedef struct {
     pmcmc_target target;

@@ -19,7 +19,7 @@ __all__ = [
     "PmcmcError", "Target", "Options", "pmcmc_create", "pmcmc_gen_noise", "pmcmc_solve",
     "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan", "pmcmc_adjoint", "pmcmc_solve_batched",
     "ChainDesc", "real_dtype", "loaded_library_path", "pmcmc_profile_enable",
-    "pmcmc_profile_get",
+    "pmcmc_profile_get", "pmcmc_scan_noalloc",
 ]
 
 
@@ -275,3 +275,20 @@ def pmcmc_profile_get() -> dict:
     p = L.pmcmc_profile()
     _check(ctx, L.load().pmcmc_profile_get(ctx, C.byref(p)))
     return {k: getattr(p, k) for k, _ in L.pmcmc_profile._fields_}
+
+
+def pmcmc_scan_noalloc(precision: str, a, b, s):
+    """The diagonal scan with static scratch and no context (for callers that cannot allocate:
+    stream capture, fixed-budget hosts, plugins under another allocator).  In place on s."""
+    T, D = s.shape
+    sd = real_dtype(precision)
+    ad = torch.bfloat16 if precision == "f32_scan_bf16" else sd
+    a, b = _dev(a, ad, "a"), _dev(b, ad, "b")
+    if not s.is_contiguous() or s.dtype != sd or not s.is_cuda:
+        raise ValueError("s must be a contiguous CUDA tensor of the precision's real type")
+    st = L.load().pmcmc_scan_noalloc(PRECISIONS[precision], T, D, _ptr(a), _ptr(b), _ptr(s),
+                                     _stream())
+    if st != 0:
+        raise PmcmcError(st, "pmcmc_scan_noalloc failed (EUNSUPPORTED: scratch beyond 8 MiB or "
+                             "D > 256)")
+    return s
