@@ -200,13 +200,16 @@ pmcmc_status pmcmc_scan(pmcmc_ctx *ctx, pmcmc_jac kind, pmcmc_precision precisio
  * as a parallel reverse scan with dense J_{t+1} = I + step H(s_t) (accepted) or I (rejected),
  * and returns dL/dtheta = sum_t lambda_t^T d f_t/d theta for theta = (step, prior_scale).
  * J is recomputed in segments when T*D*D reals exceed jac_budget_bytes (0 = no limit).
- * Only PMCMC_MALA.  s: the converged trajectory; acc: its T decisions (device bytes).
- * grad_out: 2 host doubles.
+ * PMCMC_MALA with LOGREG (D <= 128 in FP32, 64 in FP64) or GAUSSIAN targets.
+ * s: the converged trajectory; acc: its T decisions (device bytes); u is not used (the
+ * decisions are given).  lambda_out (T x D device reals, may be NULL) receives lambda.
+ * grad_out: 2 host doubles, dL/dstep and dL/dprior_scale (zero for Gaussian targets).
  */
 pmcmc_status pmcmc_adjoint(pmcmc_ctx *ctx, const pmcmc_target *target, const pmcmc_options *opt,
                            int T, const void *s0, const void *s, const unsigned char *acc,
                            const void *xi, const double *u, const void *dL_ds,
-                           size_t jac_budget_bytes, double *grad_out, void *stream);
+                           size_t jac_budget_bytes, void *lambda_out, double *grad_out,
+                           void *stream);
 
 /*
  * The diagonal scan of pmcmc_scan (kind PMCMC_JAC_DIAG) without any allocation and without a

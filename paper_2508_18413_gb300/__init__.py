@@ -19,7 +19,7 @@ __all__ = [
     "PmcmcError", "Target", "Options", "pmcmc_create", "pmcmc_gen_noise", "pmcmc_solve",
     "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan", "pmcmc_adjoint", "pmcmc_solve_batched",
     "ChainDesc", "real_dtype", "loaded_library_path", "pmcmc_profile_enable",
-    "pmcmc_profile_get", "pmcmc_scan_noalloc",
+    "pmcmc_profile_get", "pmcmc_scan_noalloc", "ChainSolve", "solve_differentiable",
 ]
 
 
@@ -215,21 +215,63 @@ def pmcmc_scan(kind: str, precision: str, a, b, s):
 
 
 def pmcmc_adjoint(target: Target, opt: Options, T: int, s0, s, acc, xi, u, dL_ds,
-                  jac_budget_bytes: int = 0):
-    """dL/d(step, prior_scale) at the fixed point with decisions held; returns a 2-tuple."""
+                  jac_budget_bytes: int = 0, want_lambda: bool = False):
+    """dL/d(step, prior_scale) at the fixed point with decisions held.
+
+    Returns (d_step, d_prior_scale) or, with want_lambda, also lambda [T, D]."""
     ctx = pmcmc_create()
     dt = real_dtype(opt.precision)
     s0, s, xi, dL_ds = (_dev(s0, dt, "s0"), _dev(s, dt, "s"), _dev(xi, dt, "xi"),
                         _dev(dL_ds, dt, "dL_ds"))
     u = _dev(u, torch.float64, "u")
     acc = _dev(acc, torch.uint8, "acc")
+    lam = torch.empty((T, target.D), dtype=dt, device="cuda") if want_lambda else None
     g = (C.c_double * 2)()
     tc, oc = target.c(dt), opt.c()
     st = L.load().pmcmc_adjoint(ctx, C.byref(tc), C.byref(oc), T, _ptr(s0), _ptr(s), _ptr(acc),
-                                _ptr(xi), _ptr(u), _ptr(dL_ds), int(jac_budget_bytes), g,
-                                _stream())
+                                _ptr(xi), _ptr(u), _ptr(dL_ds), int(jac_budget_bytes), _ptr(lam),
+                                g, _stream())
     _check(ctx, st)
+    if want_lambda:
+        return float(g[0]), float(g[1]), lam
     return float(g[0]), float(g[1])
+
+
+class ChainSolve(torch.autograd.Function):
+    """s = fixed point of the chain as a differentiable function of (step, prior_scale).
+
+    Forward: pmcmc_solve, then one linearisation pass at the solution for the accept decisions.
+    Backward: pmcmc_adjoint with those decisions held (the chain is piecewise smooth in the
+    parameters; the gradient is that of the piece the solution lies on)."""
+
+    @staticmethod
+    def forward(ctx, step, prior_scale, target, opt, T, s0, xi, u, jac_budget_bytes):
+        import dataclasses
+        o = dataclasses.replace(opt, step=float(step))
+        t = dataclasses.replace(target, prior_scale=float(prior_scale))
+        s, res = pmcmc_solve(t, o, T, s0, xi=xi, u=u)
+        _, _, acc, _ = pmcmc_linearize(t, dataclasses.replace(o, jac="zero"), T, s0, s, xi, u,
+                                       want_jac=False)
+        ctx.save_for_backward(s, acc)
+        ctx.meta = (t, o, T, s0, xi, u, jac_budget_bytes)
+        ctx.result = res
+        return s
+
+    @staticmethod
+    def backward(ctx, grad_s):
+        s, acc = ctx.saved_tensors
+        t, o, T, s0, xi, u, budget = ctx.meta
+        ge, gs = pmcmc_adjoint(t, o, T, s0, s, acc, xi, u, grad_s.contiguous(), budget)
+        dev = grad_s.device
+        return (torch.tensor(ge, dtype=torch.float64, device=dev),
+                torch.tensor(gs, dtype=torch.float64, device=dev),
+                None, None, None, None, None, None, None)
+
+
+def solve_differentiable(target: Target, opt: Options, T: int, s0, xi, u, step, prior_scale,
+                         jac_budget_bytes: int = 0):
+    """Solve the chain with `step` and `prior_scale` as differentiable torch scalars."""
+    return ChainSolve.apply(step, prior_scale, target, opt, T, s0, xi, u, jac_budget_bytes)
 
 
 @dataclass

@@ -94,7 +94,7 @@ def load(path: str = LIB_PATH):
     lib.pmcmc_scan.argtypes = [vp, i, i, i, i, vp, vp, vp, vp]
     lib.pmcmc_scan.restype = st
     lib.pmcmc_adjoint.argtypes = [vp, C.POINTER(pmcmc_target), C.POINTER(pmcmc_options), i, vp,
-                                  vp, vp, vp, vp, vp, C.c_size_t, C.POINTER(d), vp]
+                                  vp, vp, vp, vp, vp, C.c_size_t, vp, C.POINTER(d), vp]
     lib.pmcmc_adjoint.restype = st
     lib.pmcmc_solve_batched.argtypes = [vp, i, C.POINTER(pmcmc_chain_desc),
                                         C.POINTER(pmcmc_options), C.POINTER(pmcmc_result), vp]
