@@ -133,6 +133,12 @@ static int grid_for(size_t n) {
     return (int)std::max<size_t>(1, std::min<size_t>(b, 152 * 8));
 }
 
+cudaError_t pad_rows_launch(void *dst, const void *src, int N, int D, int Npad, int DP, int esz,
+                            cudaStream_t st) {
+    pad_rows_kernel<<<grid_for((size_t)Npad * DP), 256, 0, st>>>(dst, src, N, D, Npad, DP, esz);
+    return cudaGetLastError();
+}
+
 }  // namespace pm
 
 // ==========================================================================================
@@ -197,6 +203,7 @@ pmcmc_status pmcmc_destroy(pmcmc_ctx *c) {
     if (!c) return PMCMC_OK;
     cudaSetDevice(c->device);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->batch_graph_exec) cudaGraphExecDestroy(c->batch_graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->ws) cudaFree(c->ws);
     if (c->ctl) cudaFree(c->ctl);

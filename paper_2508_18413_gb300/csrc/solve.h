@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
+#include <utility>
 
 #include "common.cuh"
 #include "eval.h"
@@ -53,6 +55,10 @@ struct pmcmc_ctx {
     int prof_on = 0;
     pmcmc_profile prof{};
     cudaEvent_t pev[6] = {};
+    // batched solver: autotuned shapes and the captured persistent launch
+    std::map<std::string, std::pair<int, int>> tune_cache;
+    std::string batch_graph_key;
+    cudaGraphExec_t batch_graph_exec = nullptr;
 };
 
 namespace pm {
@@ -68,6 +74,8 @@ pmcmc_status solve_par_leapfrog(pmcmc_ctx *c, const pmcmc_target *tg, const pmcm
                                 int T, const void *s0, const void *xi, const double *u,
                                 void *s_out, pmcmc_result *res, void *stream);
 pmcmc_status set_error(pmcmc_ctx *c, pmcmc_status st, const char *msg);
+cudaError_t pad_rows_launch(void *dst, const void *src, int N, int D, int Npad, int DP, int esz,
+                            cudaStream_t st);
 
 // Profiling helpers: count a launch; bracket a timed launch (slot 0 eval, 1 jac, 2 scan).
 inline void prof_count(pmcmc_ctx *c, int n = 1) {
