@@ -33,16 +33,17 @@ METRIC = "MCMC samples/s to converged fixed point (tol stated) on 1 GB300 vs seq
 UNIT = "samples/s"
 WL = W.C2
 CLIP = 1            # clip J to [-1, 1] (Appendix B.4): the step 0.01 makes I + eps H expanding
-JAC = "diag"        # quasi-DEER with the exact diagonal
+JAC = "diag"        # quasi-DEER with the exact diagonal (of the held-gate Jacobian by default)
 WORKLOAD = (f"{WL.name}: MALA on synthetic logistic regression (N={WL.N}, D={WL.D}), "
             f"T={WL.T}, step {WL.step}, FP32, quasi-DEER exact diagonal, clip, tol {WL.tol}")
 
 # FP32 FMA peak of the GB300 (no tensor cores): 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# Algorithmic flops of one evaluate-and-linearise launch (MALA, exact diagonal, gate term):
-# per timestep 2 gradients (2 N D MACs each), diag(X^T W X) (N D), two Hessian-vector products
-# (2 N D each) = 9 N D MACs = 18 N D flops.
-ALG_FLOPS_PER_T = 18 * WL.N * WL.D
+# Algorithmic flops of one evaluate-and-linearise launch (MALA, exact diagonal), per timestep:
+# 2 gradients (2 N D MACs each) and diag(X^T W X) (N D MACs) = 5 N D MACs = 10 N D flops; with
+# the stop-gradient gate term add two Hessian-vector products (2 N D MACs each): 18 N D flops.
+def alg_flops_per_t(gate_grad: int) -> int:
+    return (18 if gate_grad else 10) * WL.N * WL.D
 # DRAM traffic of one evaluate-and-linearise launch from the committed ncu capture
 # (profiles/eval_logreg_c2.md); None until that capture exists for the current kernel.
 EVAL_TRAFFIC_BYTES = None
@@ -56,6 +57,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-variants", action="store_true", help="skip the dense-Newton line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c1", "c3_diag", "c3_bf16", "c3_block", "c4", "c5",
+                             "scan_sweep"],
+                    help="c2 (default) is the headline line; the others measure the other "
+                         "configurations")
+    ap.add_argument("--gate-grad", type=int, default=0,
+                    help="1: the stop-gradient gate term of Section 3.2 in J")
     return ap.parse_args()
 
 
@@ -193,7 +201,7 @@ def run_ours(args):
     s0 = torch.zeros(WL.D, dtype=torch.float32, device=dev)
     tgt = P.Target("logreg", WL.D, X=Xd, y=yd, prior_scale=1.0)
     opt = P.Options(sampler="mala", step=WL.step, jac=JAC, precision="f32", atol=WL.tol,
-                    clip=CLIP)
+                    clip=CLIP, gate_grad=args.gate_grad)
     s_out = torch.empty((WL.T, WL.D), dtype=torch.float32, device=dev)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2
 
@@ -208,7 +216,6 @@ def run_ours(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    P.pmcmc_profile_enable(True)
     stream = torch.cuda.current_stream()
     step_ms, results = [], []
     barrier()
@@ -222,20 +229,29 @@ def run_ours(args):
         step_ms.append(e0.elapsed_time(e1))
         results.append(res)
     barrier()
+    clk = clocks.stop()
+    # kernel durations: the same solves with per-launch CUDA events (host-driven loop)
+    P.pmcmc_profile_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        P.pmcmc_solve(tgt, opt, WL.T, s0, xi=xid, u=ud, s_out=s_out)
+    torch.cuda.synchronize()
     prof = P.pmcmc_profile_get()
     P.pmcmc_profile_enable(False)
-    clk = clocks.stop()
+    # launches inside the timed region: one evaluate per iteration plus one per solve, one
+    # scan per iteration, one control kernel per evaluate, and the solve's set-up kernels
+    launches_timed = sum(3 * r["iters"] + 2 + 5 for r in results)
 
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-        n = torch.tensor([prof["launches"]], device=dev, dtype=torch.float64)
+        n = torch.tensor([launches_timed], device=dev, dtype=torch.float64)
         dist.all_reduce(n, op=dist.ReduceOp.SUM)
         launches = int(n.item())
     else:
-        launches = int(prof["launches"])
+        launches = int(launches_timed)
     value = world * WL.T / (ms / 1000.0)
 
     # --- end to end through the public API with host buffers (pinned) ---------------------
@@ -286,7 +302,7 @@ def run_ours(args):
     dense = None
     if rank == 0 and not args.no_variants:
         optd = P.Options(sampler="mala", step=WL.step, jac="dense", precision="f32", atol=WL.tol,
-                         clip=CLIP)
+                         clip=CLIP, max_iters=300)
         P.pmcmc_solve(tgt, optd, WL.T, s0, xi=xid, u=ud, s_out=s_out)
         torch.cuda.synchronize()
         flush.zero_()
@@ -312,14 +328,15 @@ def run_ours(args):
                          f"{el:.1f} s"}
 
     avg_eval_ms = prof["eval_ms"] / max(1, prof["eval_launches"])
-    achieved = ALG_FLOPS_PER_T * WL.T / (avg_eval_ms / 1000.0) / 1e12
+    achieved = alg_flops_per_t(args.gate_grad) * WL.T / (avg_eval_ms / 1000.0) / 1e12
     last = results[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": WL.N, "D": WL.D, "T": WL.T, "step": WL.step,
-                   "jac": JAC, "clip": CLIP, "tol": WL.tol,
+                   "jac": JAC, "clip": CLIP, "gate_grad": args.gate_grad, "tol": WL.tol,
+                   "newton_loop": "CUDA graph, conditional WHILE node (device-side)",
                    "l2": "flushed before every timed step (512 MB write)",
                    "parallelism": f"{world} independent chain(s), one per GPU"},
         "newton_iters": last["iters"], "accept_rate": last["accept_rate"],
@@ -332,6 +349,8 @@ def run_ours(args):
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": EVAL_TRAFFIC_BYTES,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "avg_launch_ms": avg_eval_ms, "launches": prof["eval_launches"],
+                     "timing": "CUDA events around each launch, stream of the launch, "
+                               f"{args.steps} profiled solves after the timed region",
                      "scan_avg_ms": prof["scan_ms"] / max(1, prof["scan_launches"])},
         "seq_gpu": None if seq_ms is None else {
             "value": WL.T / (seq_ms / 1000.0), "unit": UNIT, "ms": seq_ms,
@@ -345,10 +364,184 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------
+# the other configurations (each prints one JSON line of its own)
+# ------------------------------------------------------------------------------------------
+def _timed(fn, steps, warmup, flush, stream, torch):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms, out = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms), out
+
+
+def run_other(args):
+    import torch
+
+    import paper_2508_18413_gb300 as P
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    line = {"workload": args.workload, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic", "higher_is_better": True}
+    wl = args.workload
+    if wl == "c1":
+        c = W.C1
+        mu, prec, _ = W.gaussian_c1()
+        xi, u = W.noise(c.T, 2, seed=0)
+        tgt = P.Target("gaussian", 2, mean=torch.tensor(mu, device=dev), prec=torch.tensor(prec, device=dev))
+        s0 = torch.zeros(2, dtype=torch.float64, device=dev)
+        xid, ud = torch.tensor(xi, device=dev), torch.tensor(u, device=dev)
+        opt = P.Options(sampler="mala", step=c.step, jac="dense", precision="f64", atol=c.tol)
+        ms, (s, res) = _timed(lambda: P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud), args.steps,
+                              args.warmup, flush, stream, torch)
+        sms, _ = _timed(lambda: P.pmcmc_seq_solve(tgt, opt, c.T, s0, xid, ud), 1, 1, flush, stream, torch)
+        line.update(config=c.name, value=c.T / (ms / 1e3), ms_per_step=ms, newton_iters=res["iters"],
+                    status=res["status"], us_per_iter=1e3 * ms / max(1, res["iters"]), dtype="f64",
+                    seq_gpu={"value": c.T / (sms / 1e3), "ms": sms, "speedup": sms / ms})
+    elif wl in ("c3_diag", "c3_bf16", "c3_block"):
+        c = W.C3
+        xi, u = W.noise(c.T, 2, seed=0, dtype=np.float32)
+        tgt = P.Target("banana", 2)
+        s0 = torch.zeros(2, dtype=torch.float32, device=dev)
+        xid, ud = torch.tensor(xi, device=dev), torch.tensor(u, device=dev)
+        if wl == "c3_block":
+            opt = P.Options(sampler="hmc_par_leapfrog", step=c.step, leapfrog_L=c.L, jac="block2",
+                            precision="f32", atol=1e-6, rtol=1e-6)
+        else:
+            opt = P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, jac="diag", clip=1,
+                            precision="f32" if wl == "c3_diag" else "f32_scan_bf16",
+                            atol=c.tol, rtol=c.rtol)
+        ms, (s, res) = _timed(lambda: P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud), args.steps,
+                              args.warmup, flush, stream, torch)
+        sopt = P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, precision="f32")
+        sms, _ = _timed(lambda: P.pmcmc_seq_solve(tgt, sopt, c.T, s0, xid, ud), 1, 1, flush, stream, torch)
+        line.update(config=f"{c.name} {wl}", value=c.T / (ms / 1e3), ms_per_step=ms,
+                    newton_iters=res["iters"], status=res["status"], accept_rate=res["accept_rate"],
+                    dtype="f32", seq_gpu={"value": c.T / (sms / 1e3), "ms": sms, "speedup": sms / ms})
+    elif wl == "c4":
+        c = W.C4
+        X, y, _ = W.blr_data(c.N, c.D, seed=0, dtype=np.float32)
+        xi, u = W.noise(c.T, c.D, seed=0, dtype=np.float32)
+        tgt = P.Target("logreg", c.D, X=torch.tensor(X, device=dev), y=torch.tensor(y, device=dev))
+        s0 = torch.zeros(c.D, dtype=torch.float32, device=dev)
+        xid, ud = torch.tensor(xi, device=dev), torch.tensor(u, device=dev)
+        opt = P.Options(sampler="mala", step=c.step, jac="diag", precision="f32", atol=c.tol, clip=1,
+                        gate_grad=0)
+        t0 = time.time()
+        s, res = P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud)
+        torch.cuda.synchronize()
+        fwd_ms = 1e3 * (time.time() - t0)
+        _, _, acc, _ = P.pmcmc_linearize(tgt, P.Options(sampler="mala", step=c.step, jac="zero",
+                                                        precision="f32"), c.T, s0, s, xid, ud,
+                                         want_jac=False)
+        dL = (2.0 * s / c.T).contiguous()
+        ams, g = _timed(lambda: P.pmcmc_adjoint(tgt, opt, c.T, s0, s, acc, xid, ud, dL),
+                        args.steps, 1, flush, stream, torch)
+        budget = 256 * 1024 * 1024
+        bms, gb = _timed(lambda: P.pmcmc_adjoint(tgt, opt, c.T, s0, s, acc, xid, ud, dL, budget),
+                         1, 0, flush, stream, torch)
+        line.update(config=c.name, forward={"ms": fwd_ms, "newton_iters": res["iters"],
+                                            "status": res["status"], "accept_rate": res["accept_rate"],
+                                            "value": c.T / (fwd_ms / 1e3)},
+                    adjoint={"ms": ams, "grad": g, "accepted": int(acc.sum().item())},
+                    adjoint_recompute={"ms": bms, "grad": gb, "jac_budget_bytes": budget},
+                    value=c.T / ((fwd_ms + ams) / 1e3), ms_per_step=fwd_ms + ams, dtype="f32")
+    elif wl == "c5":
+        chains = W.batched_mix(512)
+        descs = []
+        total = 0
+        for ch in chains:
+            xi, u = W.noise(ch.T, ch.D, seed=ch.noise_seed, dtype=np.float32)
+            if ch.target == "gaussian":
+                tg = P.Target("gaussian", ch.D, mean=torch.tensor(ch.mu, dtype=torch.float32, device=dev),
+                              prec=torch.tensor(ch.prec, dtype=torch.float32, device=dev))
+            else:
+                tg = P.Target("logreg", ch.D, X=torch.tensor(ch.X, dtype=torch.float32, device=dev),
+                              y=torch.tensor(ch.y, dtype=torch.float32, device=dev))
+            descs.append(P.ChainDesc(tg, ch.sampler, ch.step, ch.L, ch.T,
+                                     torch.zeros(ch.D, dtype=torch.float32, device=dev),
+                                     torch.tensor(xi, device=dev), torch.tensor(u, device=dev),
+                                     torch.empty((ch.T, ch.D), dtype=torch.float32, device=dev)))
+            total += ch.T
+        opt = P.Options(jac="diag", precision="f32_scan_bf16", atol=1e-5, rtol=1e-5, clip=1)
+        ms, res = _timed(lambda: P.pmcmc_solve_batched(descs, opt), args.steps, args.warmup,
+                         flush, stream, torch)
+        iters = [r["iters"] for r in res]
+        # sequential GPU loop: the chains one after another would take sum of their times; run
+        # each chain's sequential kernel on its own stream so they overlap on the device
+        streams = [torch.cuda.Stream() for _ in range(16)]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i, d in enumerate(descs):
+            st = streams[i % len(streams)]
+            st.wait_event(e0)
+            with torch.cuda.stream(st):
+                so = P.Options(sampler=d.sampler, step=d.step, leapfrog_L=d.leapfrog_L, precision="f32")
+                P.pmcmc_seq_solve(d.target, so, d.T, d.s0, d.xi, d.u)
+        for st in streams:
+            stream.wait_stream(st)
+        e1.record(stream)
+        e1.synchronize()
+        sms = e0.elapsed_time(e1)
+        line.update(config="512 mixed chains (MALA/HMC L=8, D in {2,8,32}, Gaussian/logistic N=500, "
+                           "T~U[1024,65536]), bfloat16 pairs", value=total / (ms / 1e3), ms_per_step=ms,
+                    samples=total, newton_iters={"max": max(iters), "mean": statistics.mean(iters)},
+                    converged=sum(r["status"] == "OK" for r in res), dtype="f32",
+                    seq_gpu={"value": total / (sms / 1e3), "ms": sms, "speedup": sms / ms,
+                             "how": "one sequential kernel per chain on 16 streams"})
+    elif wl == "scan_sweep":
+        rows = []
+        peak = _measured_hbm()
+        for prec in ("f32", "f32_scan_bf16"):
+            for k in range(20, 29, 2):
+                n = 1 << k
+                D = 8
+                T = n // D
+                sd = torch.float32
+                ad = torch.bfloat16 if prec == "f32_scan_bf16" else sd
+                a = (torch.rand((T, D), device=dev) * 1.8 - 0.9).to(ad)
+                b = torch.randn((T, D), device=dev).to(ad)
+                sv = torch.randn((T, D), device=dev, dtype=sd)
+                ms, _ = _timed(lambda: P.pmcmc_scan("diag", prec, a, b, sv), args.steps, args.warmup,
+                               flush, stream, torch)
+                bytes_ = n * (a.element_size() * 2 + 8)
+                gbs = bytes_ / (ms / 1e3) / 1e9
+                rows.append({"precision": prec, "elements": n, "T": T, "D": D, "ms": ms,
+                             "GB/s": gbs, "frac_of_measured_hbm": gbs / peak})
+                del a, b, sv
+        line.update(config="diagonal scan alone, a ~ U(-0.9, 0.9), b ~ N(0, 1), D = 8",
+                    unit="GB/s", rows=rows, hbm_peak_measured=peak)
+    line["clocks"] = clocks.stop()
+    print(json.dumps(line), flush=True)
+
+
+def _measured_hbm():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        return 6800.0  # fallback figure
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "c2":
+        run_other(args)
     else:
         run_ours(args)
 

@@ -204,6 +204,7 @@ pmcmc_status pmcmc_destroy(pmcmc_ctx *c) {
     cudaSetDevice(c->device);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->batch_graph_exec) cudaGraphExecDestroy(c->batch_graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->ws) cudaFree(c->ws);
     if (c->ctl) cudaFree(c->ctl);
@@ -449,6 +450,116 @@ extern "C" pmcmc_status pmcmc_solve(pmcmc_ctx *c, const pmcmc_target *tg,
 
 namespace pm {
 
+// Device-side control of the Newton loop (Algorithm 1): decides convergence from the residual
+// statistics of the evaluation just finished, keeps them for the host, and sets the WHILE
+// condition of the graph (1: run the scan and another iteration; 0: stop).
+__global__ void loop_ctl_kernel(CtlBlock *c, cudaGraphConditionalHandle h, double atol,
+                                int max_iters) {
+    EvalStats &s = c->stats[0];
+    EvalStats &keep = c->stats[1];
+    keep.err = s.err;
+    keep.rmax = s.rmax;
+    keep.min_margin = s.min_margin;
+    keep.accepts = s.accepts;
+    const bool conv = ord_decode(s.err) <= atol;
+    if (c->nonfinite_input || conv || c->iter >= max_iters || c->scan.timeout) {
+        c->converged = conv && !c->nonfinite_input;
+        c->skip = 1;
+        cudaGraphSetConditional(h, 0);
+    } else {
+        c->iter += 1;
+        c->skip = 0;
+        s.err = kOrdNegInf;
+        s.rmax = 0x8000000000000000ull;
+        s.min_margin = 0xfff0000000000000ull;
+        s.accepts = 0;
+        cudaGraphSetConditional(h, 1);
+    }
+}
+
+__global__ void loop_init_kernel(CtlBlock *c) {
+    c->iter = 0;
+    c->skip = 0;
+    c->converged = 0;
+    EvalStats &s = c->stats[0];
+    s.err = kOrdNegInf;
+    s.rmax = 0x8000000000000000ull;
+    s.min_margin = 0xfff0000000000000ull;
+    s.accepts = 0;
+    s.resets = 0;
+    s.dmax = 0x8000000000000000ull;
+}
+
+// Build (or reuse) the graph  [ WHILE { evaluate; control; scan } ]  for this solve.
+static pmcmc_status build_loop_graph(pmcmc_ctx *c, const std::string &key, const pmcmc_target *tg,
+                                     const pmcmc_options *o, const EvalArgs &A, const Plan &p,
+                                     const ScanWork &w, void *s_out, const void *s0, int max_iters,
+                                     unsigned int spin) {
+    if (c->graph_exec && c->graph_key == key) return PMCMC_OK;
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_key.clear();
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return PMCMC_ECUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return PMCMC_ECUDA;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t cs = c->cap_stream;
+        ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const bool f64 = o->precision == PMCMC_F64;
+            cudaError_t e = cudaSuccess;
+            if (tg->kind == PMCMC_LOGREG) {
+                e = launch_eval_logreg(A, cs);
+                if (e == cudaSuccess && o->jac == PMCMC_JAC_DENSE) e = launch_logreg_dense_jac(A, cs);
+            } else {
+                e = launch_eval_small(A, cs);
+            }
+            if (e == cudaSuccess) {
+                loop_ctl_kernel<<<1, 1, 0, cs>>>(c->ctl, h, o->atol, max_iters);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                if (o->jac == PMCMC_JAC_DENSE)
+                    e = launch_scan_dense(f64, A.T, A.D, p.tile_t, A.a_out, A.b_out, s_out, s0, w,
+                                          A.stats, &c->ctl->skip, spin, cs);
+                else
+                    e = launch_scan_diag(f64, A.bf16 ? 1 : 0, A.T, A.D, p.tile_t, A.a_out, A.b_out,
+                                         s_out, s0, w, A.stats, &c->ctl->skip, spin, cs);
+            }
+            cudaGraph_t out = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(cs, &out);
+            ok = e == cudaSuccess && ce == cudaSuccess;
+        }
+    }
+    cudaGraphExec_t ge = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return PMCMC_EUNSUPPORTED;
+    }
+    c->graph = g;
+    c->graph_exec = ge;
+    c->graph_key = key;
+    return PMCMC_OK;
+}
+
 pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
                           const void *s0, const void *s_init, const void *xi, const double *u,
                           void *s_out, pmcmc_result *res, void *stream) {
@@ -530,10 +641,51 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     const unsigned int spin = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
     const double atol = o->atol;
 
+    CtlBlock *h = c->host_ctl;
+    if (!c->prof_on && !c->no_graph) {
+        char kb[768];
+        snprintf(kb, sizeof(kb),
+                 "%llu|%d|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%d|%.17g|%d|%d|%.17g|%.17g|%d|%u|%llu|%u|"
+                 "%p|%p|%p|%p|%p|%p|%p|%p|%p",
+                 c->ws_generation, T, D, tg->N, (int)tg->kind, (int)o->sampler, o->leapfrog_L,
+                 (int)o->jac, o->step, tg->prior_scale, (int)o->precision, o->damping, o->clip,
+                 o->gate_grad, o->atol, o->rtol, max_iters, spin, o->seed, o->chain_id, s0, s_out,
+                 xi, (const void *)u, tg->mean, tg->prec, tg->X, tg->y, (void *)base);
+        pmcmc_status gs = build_loop_graph(c, kb, tg, o, A, p, w, s_out, s0, max_iters, spin);
+        if (gs == PMCMC_OK) {
+            PM_CUDA(c, cudaEventRecord(c->ev0, st));
+            loop_init_kernel<<<1, 1, 0, st>>>(c->ctl);
+            PM_CUDA(c, cudaGetLastError());
+            PM_CUDA(c, cudaGraphLaunch(c->graph_exec, st));
+            PM_CUDA(c, cudaEventRecord(c->ev1, st));
+            PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(c, cudaStreamSynchronize(st));
+            float gms = 0.f;
+            cudaEventElapsedTime(&gms, c->ev0, c->ev1);
+            if (h->nonfinite_input) return fail(c, PMCMC_ENAN, "s0 or the initial guess is not finite");
+            pmcmc_status status = h->converged ? PMCMC_OK : PMCMC_NOT_CONVERGED;
+            if (h->scan.timeout) {
+                unsigned int zero = 0;
+                cudaMemcpy(&c->ctl->scan.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+                status = PMCMC_ETIMEOUT;
+                fail(c, status, "a look-back wait in the scan ran out");
+            }
+            if (res) {
+                res->iters = h->iter;
+                res->status = status;
+                res->max_residual = ord_decode(h->stats[1].rmax);
+                res->accept_rate = (double)h->stats[1].accepts / (double)T;
+                res->min_margin = ord_decode(h->stats[1].min_margin);
+                res->nonfinite_resets = (int)h->stats[0].resets;
+                res->elapsed_ms = gms;
+            }
+            return status;
+        }
+        c->no_graph = 1;  // conditional graphs refused: use the host-driven loop from now on
+    }
     PM_CUDA(c, cudaEventRecord(c->ev0, st));
     int it = 0;
     bool converged = false;
-    CtlBlock *h = c->host_ctl;
     for (;;) {
         PM_CUDA(c, cudaMemcpyAsync(&c->ctl->iter, &it, sizeof(int), cudaMemcpyHostToDevice, st));
         stats_reset_kernel<<<1, 32, 0, st>>>(stats, 1);

@@ -46,8 +46,11 @@ struct pmcmc_ctx {
     pm::CtlBlock *ctl = nullptr;       // device
     pm::CtlBlock *host_ctl = nullptr;  // pinned host mirror
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr;          // device-side Newton loop (conditional WHILE node)
     cudaGraphExec_t graph_exec = nullptr;
+    std::string graph_key;
+    cudaStream_t cap_stream = nullptr;
+    int no_graph = 0;
     unsigned long long flags_generation = ~0ull;
     size_t flags_offset = 0, flags_zeroed = 0;
     unsigned long long resets_accum = 0;

@@ -423,3 +423,29 @@ def test_lookback_wait_bound_returns_timeout_and_context_recovers():
                            u=ug[:T2].contiguous())
     assert res["status"] == "OK"
     np.testing.assert_allclose(npy(s), ref, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["mala_logreg", "hmc_banana"])
+def test_device_loop_and_host_loop_agree(kind):
+    """The graph-resident Newton loop (conditional WHILE node) and the host-driven loop used
+    while profiling run the same kernels: identical iterates and iteration counts."""
+    T = 900
+    if kind == "mala_logreg":
+        ot, gt = logreg_pair(150, 6, seed=4, dt=torch.float32)
+        sampler, eps, L, clip = "mala", 0.01, 0, 1
+    else:
+        ot, gt = banana_pair()
+        sampler, eps, L, clip = "hmc", 0.05, 16, 1
+    xi, u = noise(T, ot.D, 6, torch.float32)
+    opt = P.Options(sampler=sampler, step=eps, leapfrog_L=L, jac="diag", precision="f32",
+                    atol=1e-5, rtol=1e-6, clip=clip)
+    s1, r1 = P.pmcmc_solve(gt, opt, T, cu(np.zeros(ot.D), torch.float32), xi=cu(xi, torch.float32),
+                           u=cu(u))
+    P.pmcmc_profile_enable(True)
+    s2, r2 = P.pmcmc_solve(gt, opt, T, cu(np.zeros(ot.D), torch.float32), xi=cu(xi, torch.float32),
+                           u=cu(u))
+    prof = P.pmcmc_profile_get()
+    P.pmcmc_profile_enable(False)
+    assert r1["iters"] == r2["iters"] and r1["status"] == r2["status"] == "OK"
+    assert torch.equal(s1, s2)
+    assert prof["eval_launches"] == r2["iters"] + 1 and prof["scan_launches"] == r2["iters"]
