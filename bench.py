@@ -62,6 +62,8 @@ def parse():
                              "scan_sweep"],
                     help="c2 (default) is the headline line; the others measure the other "
                          "configurations")
+    ap.add_argument("--basis", action="store_true",
+                    help="solve in the eigenbasis of X^T X (Section 3.4 reparameterisation)")
     ap.add_argument("--gate-grad", type=int, default=0,
                     help="1: the stop-gradient gate term of Section 3.2 in J")
     return ap.parse_args()
@@ -199,7 +201,11 @@ def run_ours(args):
     xid = torch.tensor(xi_h, device=dev)
     ud = torch.tensor(u_h, device=dev)
     s0 = torch.zeros(WL.D, dtype=torch.float32, device=dev)
-    tgt = P.Target("logreg", WL.D, X=Xd, y=yd, prior_scale=1.0)
+    Qd = None
+    if args.basis:
+        _, Qh = np.linalg.eigh(X.astype(np.float64).T @ X.astype(np.float64))
+        Qd = torch.tensor(Qh.astype(np.float32), device=dev)
+    tgt = P.Target("logreg", WL.D, X=Xd, y=yd, prior_scale=1.0, Q=Qd)
     opt = P.Options(sampler="mala", step=WL.step, jac=JAC, precision="f32", atol=WL.tol,
                     clip=CLIP, gate_grad=args.gate_grad)
     s_out = torch.empty((WL.T, WL.D), dtype=torch.float32, device=dev)
@@ -262,7 +268,7 @@ def run_ours(args):
     s0h = torch.zeros(WL.D, dtype=torch.float32).pin_memory()
     outh = torch.empty((WL.T, WL.D), dtype=torch.float32).pin_memory()
     Xe, ye, xie, ue, s0e = (torch.empty_like(t, device=dev) for t in (Xh, yh, xih, uh, s0h))
-    tgt_e = P.Target("logreg", WL.D, X=Xe, y=ye, prior_scale=1.0)
+    tgt_e = P.Target("logreg", WL.D, X=Xe, y=ye, prior_scale=1.0, Q=Qd)
     h2d = sum(t.numel() * t.element_size() for t in (Xh, yh, xih, uh, s0h))
     d2h = outh.numel() * outh.element_size()
     e2e_ms = []
@@ -336,6 +342,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": WL.N, "D": WL.D, "T": WL.T, "step": WL.step,
                    "jac": JAC, "clip": CLIP, "gate_grad": args.gate_grad, "tol": WL.tol,
+                   "basis": "eigenvectors of X^T X" if args.basis else "identity",
                    "newton_loop": "CUDA graph, conditional WHILE node (device-side)",
                    "l2": "flushed before every timed step (512 MB write)",
                    "parallelism": f"{world} independent chain(s), one per GPU"},
@@ -435,7 +442,9 @@ def run_other(args):
         c = W.C4
         X, y, _ = W.blr_data(c.N, c.D, seed=0, dtype=np.float32)
         xi, u = W.noise(c.T, c.D, seed=0, dtype=np.float32)
-        tgt = P.Target("logreg", c.D, X=torch.tensor(X, device=dev), y=torch.tensor(y, device=dev))
+        _, Qh = np.linalg.eigh(X.astype(np.float64).T @ X.astype(np.float64))
+        tgt = P.Target("logreg", c.D, X=torch.tensor(X, device=dev), y=torch.tensor(y, device=dev),
+                       Q=torch.tensor(Qh.astype(np.float32), device=dev))
         s0 = torch.zeros(c.D, dtype=torch.float32, device=dev)
         xid, ud = torch.tensor(xi, device=dev), torch.tensor(u, device=dev)
         opt = P.Options(sampler="mala", step=c.step, jac="diag", precision="f32", atol=c.tol, clip=1,
@@ -466,11 +475,15 @@ def run_other(args):
         for ch in chains:
             xi, u = W.noise(ch.T, ch.D, seed=ch.noise_seed, dtype=np.float32)
             if ch.target == "gaussian":
+                _, Qh = np.linalg.eigh(ch.prec)
                 tg = P.Target("gaussian", ch.D, mean=torch.tensor(ch.mu, dtype=torch.float32, device=dev),
-                              prec=torch.tensor(ch.prec, dtype=torch.float32, device=dev))
+                              prec=torch.tensor(ch.prec, dtype=torch.float32, device=dev),
+                              Q=torch.tensor(Qh, dtype=torch.float32, device=dev))
             else:
+                _, Qh = np.linalg.eigh(ch.X.T @ ch.X)
                 tg = P.Target("logreg", ch.D, X=torch.tensor(ch.X, dtype=torch.float32, device=dev),
-                              y=torch.tensor(ch.y, dtype=torch.float32, device=dev))
+                              y=torch.tensor(ch.y, dtype=torch.float32, device=dev),
+                              Q=torch.tensor(Qh, dtype=torch.float32, device=dev))
             descs.append(P.ChainDesc(tg, ch.sampler, ch.step, ch.L, ch.T,
                                      torch.zeros(ch.D, dtype=torch.float32, device=dev),
                                      torch.tensor(xi, device=dev), torch.tensor(u, device=dev),
@@ -498,7 +511,8 @@ def run_other(args):
         e1.synchronize()
         sms = e0.elapsed_time(e1)
         line.update(config="512 mixed chains (MALA/HMC L=8, D in {2,8,32}, Gaussian/logistic N=500, "
-                           "T~U[1024,65536]), bfloat16 pairs", value=total / (ms / 1e3), ms_per_step=ms,
+                           "T~U[1024,65536]), bfloat16 pairs, eigenbasis of P or X^T X per chain",
+                    value=total / (ms / 1e3), ms_per_step=ms,
                     samples=total, newton_iters={"max": max(iters), "mean": statistics.mean(iters)},
                     converged=sum(r["status"] == "OK" for r in res), dtype="f32",
                     seq_gpu={"value": total / (sms / 1e3), "ms": sms, "speedup": sms / ms,

@@ -88,6 +88,12 @@ typedef struct {
     const void *X;       /* LOGREG: N x D design, row-major, device */
     const void *y;       /* LOGREG: N labels in {0, 1}, reals, device */
     double prior_scale;  /* LOGREG: prior N(0, prior_scale^2 I) */
+    const void *Q;       /* optional D x D orthogonal basis, row-major, device; the Newton solve
+                            runs in z = Q^T s (Section 3.4, Eq. 10), so a diagonal Jacobian is
+                            taken of Q^T J Q.  The chain is unchanged: the noise is rotated with
+                            it (xi' = Q^T xi), which leaves MALA and HMC exactly equivariant.
+                            Used by pmcmc_solve and pmcmc_solve_batched for GAUSSIAN and LOGREG
+                            targets; NULL = identity. */
 } pmcmc_target;
 
 typedef struct {

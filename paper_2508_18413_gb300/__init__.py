@@ -90,14 +90,15 @@ class Target:
     X: torch.Tensor | None = None
     y: torch.Tensor | None = None
     prior_scale: float = 1.0
+    Q: torch.Tensor | None = None   # optional orthogonal basis (Section 3.4)
 
     def c(self, dtype) -> L.pmcmc_target:
         self._keep = [_dev(t, dtype, n) for t, n in ((self.mean, "mean"), (self.prec, "prec"),
-                                                    (self.X, "X"), (self.y, "y"))]
-        m, p, x, y = self._keep
+                                                    (self.X, "X"), (self.y, "y"), (self.Q, "Q"))]
+        m, p, x, y, q = self._keep
         N = 0 if x is None else x.shape[0]
         return L.pmcmc_target(TARGETS[self.kind], self.D, N, _ptr(m), _ptr(p), _ptr(x), _ptr(y),
-                              float(self.prior_scale))
+                              float(self.prior_scale), _ptr(q))
 
 
 @dataclass

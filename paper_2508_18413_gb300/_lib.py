@@ -22,7 +22,7 @@ PRECISIONS = {"f64": 0, "f32": 1, "f32_scan_bf16": 2}
 class pmcmc_target(C.Structure):
     _fields_ = [("kind", C.c_int), ("D", C.c_int), ("N", C.c_int),
                 ("mean", C.c_void_p), ("prec", C.c_void_p), ("X", C.c_void_p),
-                ("y", C.c_void_p), ("prior_scale", C.c_double)]
+                ("y", C.c_void_p), ("prior_scale", C.c_double), ("Q", C.c_void_p)]
 
 
 class pmcmc_options(C.Structure):

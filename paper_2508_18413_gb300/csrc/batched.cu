@@ -831,8 +831,7 @@ static pmcmc_status run_batched(pmcmc_ctx *c, int B, const pmcmc_chain_desc *cha
     // capture the persistent launch into a CUDA graph once per (workspace, chains, shape) and
     // replay it; fall back to a direct launch if the capture is refused
     char key[128];
-    snprintf(key, sizeof(key), "%llu:%p:%d:%d:%d", c->ws_generation, (void *)chains, B, grid,
-             tune.small_tile);
+    snprintf(key, sizeof(key), "%llu:%d:%d:%d", c->ws_generation, B, grid, tune.small_tile);
     bool launched = false;
     if (c->batch_graph_key == key && c->batch_graph_exec) {
         launched = cudaGraphLaunch(c->batch_graph_exec, st) == cudaSuccess;
@@ -919,8 +918,62 @@ extern "C" pmcmc_status pmcmc_solve_batched(pmcmc_ctx *c, int B, const pmcmc_cha
     }
     PM_CUDA_B(cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
-    BatchTune tune = batch_tune_lookup(c, B, chains, o, st);
-    return run_batched(c, B, chains, o, res, st, tune, nullptr, true);
+    // chains with an orthogonal basis Q (Section 3.4) are solved in rotated coordinates
+    bool any_q = false;
+    for (int i = 0; i < B; i++) any_q = any_q || chains[i].target.Q;
+    std::vector<pmcmc_chain_desc> rc;
+    const pmcmc_chain_desc *use = chains;
+    if (any_q) {
+        rc.assign(chains, chains + B);
+        Carve cv;
+        std::vector<size_t> off(B);
+        for (int i = 0; i < B; i++) {
+            if (!chains[i].target.Q) continue;
+            const pmcmc_chain_desc &d = chains[i];
+            const int D = d.target.D;
+            off[i] = cv.take(sizeof(float) * ((size_t)2 * d.T * D + 2 * D + (size_t)D * D +
+                                              (d.target.kind == PMCMC_LOGREG ? (size_t)d.target.N * D : 0)));
+        }
+        pmcmc_status ps = aux_reserve(c, cv.used);
+        if (ps != PMCMC_OK) return ps;
+        for (int i = 0; i < B; i++) {
+            if (!chains[i].target.Q) continue;
+            const pmcmc_chain_desc &d = chains[i];
+            const int D = d.target.D;
+            float *p = (float *)((char *)c->aux + off[i]);
+            float *xi = p, *z = xi + (size_t)d.T * D, *s0 = z + (size_t)d.T * D, *mu = s0 + D;
+            float *P = mu + D, *X = P + (size_t)D * D;
+            PM_CUDA_B(rot_rows(xi, d.xi, d.target.Q, d.T, D, true, false, st));
+            PM_CUDA_B(rot_rows(s0, d.s0, d.target.Q, 1, D, true, false, st));
+            pmcmc_chain_desc &r = rc[i];
+            r.xi = xi;
+            r.s0 = s0;
+            r.s_out = z;
+            r.target.Q = nullptr;
+            if (d.target.kind == PMCMC_GAUSSIAN) {
+                PM_CUDA_B(rot_rows(mu, d.target.mean, d.target.Q, 1, D, true, false, st));
+                PM_CUDA_B(rot_sym(P, d.target.prec, d.target.Q, D, false, st));
+                r.target.mean = mu;
+                r.target.prec = P;
+            } else if (d.target.kind == PMCMC_LOGREG) {
+                PM_CUDA_B(rot_rows(X, d.target.X, d.target.Q, d.target.N, D, true, false, st));
+                r.target.X = X;
+            } else {
+                return set_error(c, PMCMC_EUNSUPPORTED, "batched: basis Q for Gaussian or logistic chains");
+            }
+        }
+        use = rc.data();
+    }
+    BatchTune tune = batch_tune_lookup(c, B, use, o, st);
+    pmcmc_status ps = run_batched(c, B, use, o, res, st, tune, nullptr, true);
+    if (any_q && ps >= 0) {
+        for (int i = 0; i < B; i++)
+            if (chains[i].target.Q)
+                PM_CUDA_B(rot_rows(chains[i].s_out, rc[i].s_out, chains[i].target.Q, chains[i].T,
+                                   chains[i].target.D, false, false, st));
+        PM_CUDA_B(cudaStreamSynchronize(st));
+    }
+    return ps;
 }
 
 namespace pm {

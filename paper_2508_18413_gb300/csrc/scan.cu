@@ -66,6 +66,62 @@ __device__ __forceinline__ unsigned int make_flag(unsigned int epoch, unsigned i
     return ((epoch & 0x3fffffffu) << 2) | state;
 }
 
+// Warp-parallel look-back for the diagonal scans (warp 0 of the CTA, D <= 32 channels).
+// Lane l examines predecessor tile jend - l; the nearest tile whose inclusive value is
+// published ends the walk; the aggregates of the tiles in between are composed with a
+// shuffle tree per channel (lower lane = later map).  Windows of 32 predecessors are examined
+// at once, so the walk costs one round of loads per 32 tiles.  Returns, in lane d < D, the
+// carry (delta at the end of tile - 1) of channel d.  Waits are bounded; a wait that runs out
+// ends the walk with a zero carry and leaves the timeout flag set.
+template <typename R>
+__device__ __forceinline__ R lookback_window(const unsigned int *flags, const R *gagg,
+                                             const R *gincl, int tile, int D,
+                                             unsigned int epoch, unsigned int spin_limit,
+                                             ScanCtl *ctl) {
+    const int lane = threadIdx.x & 31;
+    R MA = R(1), MB = R(0), carry = R(0);
+    int jend = tile - 1;
+    for (;;) {
+        const int j = jend - lane;
+        unsigned int st = kFlagIncl;
+        if (j >= 0) st = wait_flag(flags, j, epoch, spin_limit, ctl);
+        const bool stop = (j < 0) || st != kFlagAgg;  // inclusive, before tile 0, or timeout
+        const unsigned int ball = __ballot_sync(0xffffffffu, stop);
+        const int k = ball ? __ffs(ball) - 1 : 32;
+        for (int d = 0; d < D; d++) {
+            R a = R(1), b = R(0);
+            if (lane < k) {
+                a = gagg[((size_t)j * 2) * D + d];
+                b = gagg[((size_t)j * 2 + 1) * D + d];
+            }
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const R oa = __shfl_down_sync(0xffffffffu, a, off);
+                const R ob = __shfl_down_sync(0xffffffffu, b, off);
+                if (lane + off < 32) {
+                    b = a * ob + b;
+                    a = a * oa;
+                }
+            }
+            const R Wa = __shfl_sync(0xffffffffu, a, 0), Wb = __shfl_sync(0xffffffffu, b, 0);
+            R iv = R(0);
+            if (k < 32) {
+                R v = R(0);
+                if (lane == k && j >= 0 && st == kFlagIncl) v = gincl[(size_t)j * D + d];
+                iv = __shfl_sync(0xffffffffu, v, k);
+            }
+            if (lane == d) {
+                MB = MA * Wb + MB;
+                MA = MA * Wa;
+                if (k < 32) carry = MA * iv + MB;
+            }
+        }
+        if (k < 32) break;
+        jend -= 32;
+    }
+    return carry;
+}
+
 }  // namespace
 
 // ==========================================================================================
@@ -221,7 +277,161 @@ scan_diag_kernel(int T, int D, int TT, const S *__restrict__ a, const S *__restr
     finish_tile(ctl, ntiles);
 }
 
+// ==========================================================================================
+// Diagonal scan, D <= 32, register resident.  A row is 32 lanes holding P = 32 / D consecutive
+// timesteps of all D channels (L = P D contiguous elements, coalesced).  Each warp owns ROWS
+// rows; a CTA (8 warps) owns a tile of 8 ROWS P timesteps.
+//   1. every lane loads its ROWS (a, b, s) elements (all loads in flight at once);
+//   2. each row is scanned across lanes with a channel-segmented shuffle scan (offsets
+//      D, 2D, 4D, ...); the row aggregate of channel d sits in lane (P - 1) D + d;
+//   3. rows are composed in order into the warp aggregate, warps into the tile aggregate;
+//   4. the tile aggregate is published and the carry found by the bounded look-back;
+//   5. rows are applied in order from the carry and s is stored.
+// ==========================================================================================
+template <typename R, typename S, int ROWS>
+__global__ void __launch_bounds__(256)
+scan_diag_rows_kernel(int T, int D, const S *__restrict__ a, const S *__restrict__ b,
+                      R *__restrict__ s, const R *__restrict__ s_reset, unsigned int *flags,
+                      R *__restrict__ gagg, R *__restrict__ gincl, ScanCtl *ctl, EvalStats *stats,
+                      const int *skip, unsigned int spin_limit) {
+    if (skip && *(volatile const int *)skip) return;
+    __shared__ unsigned int s_tile, s_epoch;
+    __shared__ R wA[8][32], wB[8][32];   // warp aggregates per channel
+    __shared__ R cin[8][32];             // carry into each warp
+    const int P = 32 / D, L = P * D;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int TT = 8 * ROWS * P;
+    const unsigned int ntiles = (unsigned int)ceil_div(T, TT);
+    const int tile = (int)take_tile(ctl, &s_tile, &s_epoch);
+    const unsigned int epoch = s_epoch;
+    const bool lane_on = lane < L;
+    const int d = lane_on ? lane % D : 0;
+    const int tsub = lane_on ? lane / D : 0;
+    const int last_lane = (P - 1) * D + d;  // lane holding the row end of channel d
+    const long long t_base = (long long)tile * TT + (long long)w * ROWS * P;
+
+    R ra[ROWS], rb[ROWS], rs[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        const long long t = t_base + (long long)r * P + tsub;
+        const bool in = lane_on && t < T;
+        const size_t e = (size_t)t * D + d;
+        ra[r] = in ? load_as<S, R>(a + e) : R(1);
+        rb[r] = in ? load_as<S, R>(b + e) : R(0);
+        rs[r] = in ? s[e] : R(0);
+    }
+    // 2. within-row inclusive scans (in place: ra, rb become the row prefixes)
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        for (int off = D; off < L; off <<= 1) {
+            const R pa = __shfl_up_sync(0xffffffffu, ra[r], off);
+            const R pb = __shfl_up_sync(0xffffffffu, rb[r], off);
+            if (lane_on && lane >= off) {
+                rb[r] = ra[r] * pb + rb[r];
+                ra[r] = ra[r] * pa;
+            }
+        }
+    }
+    // 3. warp aggregate per channel: rows composed in order
+    R WA = R(1), WB = R(0);
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        const R ea = __shfl_sync(0xffffffffu, ra[r], last_lane);
+        const R eb = __shfl_sync(0xffffffffu, rb[r], last_lane);
+        WB = ea * WB + eb;
+        WA = ea * WA;
+    }
+    if (lane < D) {
+        wA[w][lane] = WA;
+        wB[w][lane] = WB;
+    }
+    __syncthreads();
+    // 4. tile aggregate, publish, look back (warp 0, one lane per channel)
+    if (w == 0) {
+        R TA = R(1), TB = R(0);
+        if (lane < D) {
+            for (int q = 0; q < 8; q++) {
+                cin[q][lane] = TB;  // exclusive (B part) before warp q, carry applied below
+                TB = wA[q][lane] * TB + wB[q][lane];
+                TA = wA[q][lane] * TA;
+            }
+            if (tile == 0) {
+                gincl[lane] = TB;
+            } else {
+                gagg[((size_t)tile * 2) * D + lane] = TA;
+                gagg[((size_t)tile * 2 + 1) * D + lane] = TB;
+            }
+            __threadfence();
+        }
+        __syncwarp();
+        if (lane == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
+        R c = R(0);
+        if (tile > 0) {
+            c = lookback_window<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl);
+            if (lane < D) {
+                gincl[(size_t)tile * D + lane] = TA * c + TB;
+                __threadfence();
+            }
+        }
+        __syncwarp();
+        if (tile > 0 && lane == 0) st_release(flags + tile, make_flag(epoch, kFlagIncl));
+        // carry into each warp: (prefix of warps < q) applied to the tile carry c
+        if (lane < D) {
+            R pa = R(1);
+            for (int q = 0; q < 8; q++) {
+                const R excl_b = cin[q][lane];
+                cin[q][lane] = pa * c + excl_b;
+                pa = wA[q][lane] * pa;
+            }
+        }
+    }
+    __syncthreads();
+    // 5. apply rows in order
+    R delta = lane_on ? cin[w][d] : R(0);
+    R dmax = R(0);
+    unsigned int resets = 0;
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        const R dl = ra[r] * delta + rb[r];
+        const long long t = t_base + (long long)r * P + tsub;
+        if (lane_on && t < T) {
+            const size_t e = (size_t)t * D + d;
+            R sn = rs[r] + dl;
+            if (!finite(sn)) {
+                sn = s_reset ? s_reset[d] : R(0);
+                resets++;
+            } else {
+                dmax = max(dmax, fabs(dl));
+            }
+            s[e] = sn;
+        }
+        delta = __shfl_sync(0xffffffffu, dl, last_lane);
+    }
+    if (stats) {
+        double dm = warp_max((double)dmax);
+        unsigned int rsum = warp_sum(resets);
+        if (lane == 0) {
+            if (dm > 0) atomic_max_d(&stats->dmax, dm);
+            if (rsum) atomicAdd(&stats->resets, (unsigned long long)rsum);
+        }
+    }
+    finish_tile(ctl, ntiles);
+}
+
+// rows per warp for the register-resident scan: fill the GPU about twice, at most 16
+static int diag_rows(int T, int D) {
+    const int P = 32 / D;
+    for (int rows : {16, 8, 4, 2})
+        if (ceil_div(T, 8 * rows * P) >= 2 * 152) return rows;
+    return 2;
+}
+
+int diag_scan_tile_rows(int T, int D) {
+    return 8 * diag_rows(T, D) * (32 / D);
+}
+
 int diag_scan_tile(int T, int D, int elem_bytes) {
+    if (D <= 32) return diag_scan_tile_rows(T, D);
     // enough tiles to fill the GPU twice over, at most ~4096 elements (FP32) per tile
     const int max_elems = elem_bytes >= 8 ? 2048 : 4096;
     int tt_max = std::max(8, (max_elems / std::max(D, 1)) / 8 * 8);
@@ -254,10 +464,38 @@ static cudaError_t run_scan_diag(int T, int D, int TT, const void *a, const void
     return cudaGetLastError();
 }
 
+template <typename R, typename S>
+static cudaError_t run_scan_rows(int T, int D, const void *a, const void *b, void *s,
+                                 const void *s_reset, const ScanWork &w, EvalStats *stats,
+                                 const int *skip, unsigned int spin, cudaStream_t st) {
+    const int rows = diag_rows(T, D);
+    const int ntiles = ceil_div(T, 8 * rows * (32 / D));
+    if (ntiles > w.max_tiles) return cudaErrorInvalidValue;
+#define PM_ROWS(N_)                                                                             \
+    if (rows == N_) {                                                                          \
+        scan_diag_rows_kernel<R, S, N_><<<ntiles, 256, 0, st>>>(                               \
+            T, D, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags, (R *)w.agg, \
+            (R *)w.incl, w.ctl, stats, skip, spin);                                            \
+        return cudaGetLastError();                                                             \
+    }
+    PM_ROWS(16)
+    PM_ROWS(8)
+    PM_ROWS(4)
+    PM_ROWS(2)
+#undef PM_ROWS
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, const void *a,
                              const void *b, void *s, const void *s_reset, const ScanWork &w,
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st) {
+    if (D <= 32) {
+        if (f64) return run_scan_rows<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+        if (storage == 1)
+            return run_scan_rows<float, __nv_bfloat16>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+        return run_scan_rows<float, float>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+    }
     if (ceil_div(T, tile_t) > w.max_tiles) return cudaErrorInvalidValue;
     if (f64) return run_scan_diag<double, double>(T, D, tile_t, a, b, s, s_reset, w, stats, skip, spin_limit, st);
     if (storage == 1)
@@ -405,7 +643,174 @@ scan_dense_kernel(int T, int D, int C, const R *__restrict__ a, const R *__restr
     finish_tile(ctl, ntiles);
 }
 
+// ==========================================================================================
+// Dense scan for D <= 4: one timestep per thread, the affine element (A, b) in registers.
+// Warp shuffle scan, block combine over 8 warps, one look-back per 256-step tile.
+// ==========================================================================================
+template <typename R, int DM>
+struct Aff {
+    R A[DM][DM], b[DM];
+};
+
+// (later) o (earlier): (A2 A1, A2 b1 + b2)
+template <typename R, int DM>
+__device__ __forceinline__ Aff<R, DM> compose(const Aff<R, DM> &l, const Aff<R, DM> &e, int D) {
+    Aff<R, DM> o;
+#pragma unroll
+    for (int i = 0; i < DM; i++) {
+        R acc = l.b[i];
+#pragma unroll
+        for (int k = 0; k < DM; k++) acc += l.A[i][k] * e.b[k];
+        o.b[i] = acc;
+#pragma unroll
+        for (int j = 0; j < DM; j++) {
+            R m = R(0);
+#pragma unroll
+            for (int k = 0; k < DM; k++) m += l.A[i][k] * e.A[k][j];
+            o.A[i][j] = m;
+        }
+    }
+    (void)D;
+    return o;
+}
+
+template <typename R, int DM>
+__device__ __forceinline__ Aff<R, DM> shfl_up_aff(const Aff<R, DM> &x, int off) {
+    Aff<R, DM> o;
+#pragma unroll
+    for (int i = 0; i < DM; i++) {
+        o.b[i] = __shfl_up_sync(0xffffffffu, x.b[i], off);
+#pragma unroll
+        for (int j = 0; j < DM; j++) o.A[i][j] = __shfl_up_sync(0xffffffffu, x.A[i][j], off);
+    }
+    return o;
+}
+
+template <typename R, int DM>
+__global__ void __launch_bounds__(256)
+scan_dense_small_kernel(int T, int D, const R *__restrict__ a, const R *__restrict__ b,
+                        R *__restrict__ s, const R *__restrict__ s_reset, unsigned int *flags,
+                        R *__restrict__ gagg, R *__restrict__ gincl, ScanCtl *ctl,
+                        EvalStats *stats, const int *skip, unsigned int spin_limit) {
+    if (skip && *(volatile const int *)skip) return;
+    __shared__ unsigned int s_tile, s_epoch;
+    __shared__ Aff<R, DM> wagg[8];
+    __shared__ R wcar[8][DM];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned int ntiles = (unsigned int)ceil_div(T, 256);
+    const int tile = (int)take_tile(ctl, &s_tile, &s_epoch);
+    const unsigned int epoch = s_epoch;
+    const int t = tile * 256 + threadIdx.x;
+    const bool in = t < T;
+    const int DD = D * D;
+    Aff<R, DM> x;
+#pragma unroll
+    for (int i = 0; i < DM; i++) {
+        x.b[i] = (in && i < D) ? b[(size_t)t * D + i] : R(0);
+#pragma unroll
+        for (int j = 0; j < DM; j++)
+            x.A[i][j] = (in && i < D && j < D) ? a[(size_t)t * DD + i * D + j] : (i == j ? R(1) : R(0));
+    }
+    // warp inclusive scan
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        Aff<R, DM> p = shfl_up_aff<R, DM>(x, off);
+        if (lane >= off) x = compose<R, DM>(x, p, D);
+    }
+    if (lane == 31) wagg[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // warp prefixes, tile aggregate, publish, look back, carries into the warps
+        Aff<R, DM> acc = wagg[0];
+        for (int q = 1; q < 8; q++) acc = compose<R, DM>(wagg[q], acc, D);
+        R c[DM];
+#pragma unroll
+        for (int i = 0; i < DM; i++) c[i] = R(0);
+        if (tile == 0) {
+            for (int i = 0; i < D; i++) gincl[i] = acc.b[i];
+            __threadfence();
+            st_release(flags, make_flag(epoch, kFlagIncl));
+        } else {
+            const size_t AGG = (size_t)DD + D;
+            for (int i = 0; i < D; i++) {
+                for (int j = 0; j < D; j++) gagg[(size_t)tile * AGG + i * D + j] = acc.A[i][j];
+                gagg[(size_t)tile * AGG + DD + i] = acc.b[i];
+            }
+            __threadfence();
+            st_release(flags + tile, make_flag(epoch, kFlagAgg));
+            int jj = tile - 1;
+            for (; jj >= 0; jj--) {
+                unsigned int st = wait_flag(flags, jj, epoch, spin_limit, ctl);
+                if (st == kFlagIncl || st == 0) break;
+            }
+            if (jj >= 0) {
+                unsigned int st = ld_acquire(flags + jj);
+                if ((st & 3u) == kFlagIncl && (st >> 2) == (epoch & 0x3fffffffu))
+                    for (int i = 0; i < D; i++) c[i] = gincl[(size_t)jj * D + i];
+            }
+            for (int m = max(jj + 1, 0); m < tile; m++) {
+                const R *Am = gagg + (size_t)m * AGG;
+                R nc[DM];
+                for (int i = 0; i < D; i++) {
+                    R v = Am[DD + i];
+                    for (int k = 0; k < D; k++) v += Am[i * D + k] * c[k];
+                    nc[i] = v;
+                }
+                for (int i = 0; i < D; i++) c[i] = nc[i];
+            }
+            for (int i = 0; i < D; i++) {
+                R v = acc.b[i];
+                for (int k = 0; k < D; k++) v += acc.A[i][k] * c[k];
+                gincl[(size_t)tile * D + i] = v;
+            }
+            __threadfence();
+            st_release(flags + tile, make_flag(epoch, kFlagIncl));
+        }
+        // carry into warp q = (warps < q) applied to c
+        for (int q = 0; q < 8; q++) {
+            for (int i = 0; i < DM; i++) wcar[q][i] = c[i];
+            R nc[DM];
+            for (int i = 0; i < D; i++) {
+                R v = wagg[q].b[i];
+                for (int k = 0; k < D; k++) v += wagg[q].A[i][k] * c[k];
+                nc[i] = v;
+            }
+            for (int i = 0; i < D; i++) c[i] = nc[i];
+        }
+    }
+    __syncthreads();
+    R dmax = R(0);
+    unsigned int resets = 0;
+    if (in) {
+#pragma unroll
+        for (int i = 0; i < DM; i++) {
+            if (i >= D) continue;
+            R dl = x.b[i];
+#pragma unroll
+            for (int k = 0; k < DM; k++) dl += x.A[i][k] * wcar[w][k];
+            R sn = s[(size_t)t * D + i] + dl;
+            if (!finite(sn)) {
+                sn = s_reset ? s_reset[i] : R(0);
+                resets++;
+            } else {
+                dmax = max(dmax, fabs(dl));
+            }
+            s[(size_t)t * D + i] = sn;
+        }
+    }
+    if (stats) {
+        double dm = warp_max((double)dmax);
+        unsigned int rs = warp_sum(resets);
+        if (lane == 0) {
+            if (dm > 0) atomic_max_d(&stats->dmax, dm);
+            if (rs) atomicAdd(&stats->resets, (unsigned long long)rs);
+        }
+    }
+    finish_tile(ctl, ntiles);
+}
+
 int dense_scan_chunk(int T, int D) {
+    if (D <= 4) return 256;  // one timestep per thread, 256 per tile
     int c = ceil_div(T, 2 * 152);
     return std::max(8, std::min(c, 64));
 }
@@ -425,6 +830,22 @@ cudaError_t launch_scan_dense(bool f64, int T, int D, int chunk, const void *a, 
                               const int *skip, unsigned int spin_limit, cudaStream_t st) {
     if (ceil_div(T, chunk) > w.max_tiles) return cudaErrorInvalidValue;
     if (D > 32) return cudaErrorInvalidValue;
+    if (D <= 4) {
+        if (chunk != 256) return cudaErrorInvalidValue;
+#define PM_DS(R_, DM_)                                                                           \
+    scan_dense_small_kernel<R_, DM_><<<ceil_div(T, 256), 256, 0, st>>>(                        \
+        T, D, (const R_ *)a, (const R_ *)b, (R_ *)s, (const R_ *)s_reset, w.flags, (R_ *)w.agg, \
+        (R_ *)w.incl, w.ctl, stats, skip, spin_limit);                                         \
+    return cudaGetLastError();
+        if (f64) {
+            if (D <= 2) { PM_DS(double, 2) }
+            PM_DS(double, 4)
+        } else {
+            if (D <= 2) { PM_DS(float, 2) }
+            PM_DS(float, 4)
+        }
+#undef PM_DS
+    }
 #define PM_DENSE(R_, DM_) \
     return run_scan_dense<R_, DM_>(T, D, chunk, a, b, s, s_reset, w, stats, skip, spin_limit, st)
     if (f64) {

@@ -207,6 +207,7 @@ pmcmc_status pmcmc_destroy(pmcmc_ctx *c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->ws) cudaFree(c->ws);
+    if (c->aux) cudaFree(c->aux);
     if (c->ctl) cudaFree(c->ctl);
     if (c->host_ctl) cudaFreeHost(c->host_ctl);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -443,6 +444,7 @@ extern "C" pmcmc_status pmcmc_solve(pmcmc_ctx *c, const pmcmc_target *tg,
         return PMCMC_OK;
     }
     PM_CUDA(c, cudaSetDevice(c->device));
+    if (tg->Q) return solve_with_basis(c, tg, o, T, s0, s_init, xi, u, s_out, res, stream);
     if (o->sampler == PMCMC_HMC_PAR_LEAPFROG)
         return solve_par_leapfrog(c, tg, o, T, s0, xi, u, s_out, res, stream);
     return newton_solve(c, tg, o, T, s0, s_init, xi, u, s_out, res, stream);

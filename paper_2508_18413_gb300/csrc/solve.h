@@ -60,6 +60,8 @@ struct pmcmc_ctx {
     cudaEvent_t pev[6] = {};
     // batched solver: autotuned shapes and the captured persistent launch
     std::map<std::string, std::pair<int, int>> tune_cache;
+    void *aux = nullptr;  // rotated copies for the orthogonal basis Q
+    size_t aux_bytes = 0;
     std::string batch_graph_key;
     cudaGraphExec_t batch_graph_exec = nullptr;
 };
@@ -77,6 +79,13 @@ pmcmc_status solve_par_leapfrog(pmcmc_ctx *c, const pmcmc_target *tg, const pmcm
                                 int T, const void *s0, const void *xi, const double *u,
                                 void *s_out, pmcmc_result *res, void *stream);
 pmcmc_status set_error(pmcmc_ctx *c, pmcmc_status st, const char *msg);
+pmcmc_status solve_with_basis(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
+                              const void *s0, const void *s_init, const void *xi, const double *u,
+                              void *s_out, pmcmc_result *res, void *stream);
+pmcmc_status aux_reserve(pmcmc_ctx *c, size_t bytes);
+cudaError_t rot_rows(void *dst, const void *src, const void *Q, long long rows, int D,
+                     bool transpose, bool f64, cudaStream_t st);
+cudaError_t rot_sym(void *out, const void *P, const void *Q, int D, bool f64, cudaStream_t st);
 cudaError_t pad_rows_launch(void *dst, const void *src, int N, int D, int Npad, int DP, int esz,
                             cudaStream_t st);
 

@@ -101,3 +101,27 @@ def test_batched_rejects_bad_chains():
         P.pmcmc_solve_batched([bad], P.Options(jac="diag", precision="f32"))
     with pytest.raises(P.PmcmcError, match="EUNSUPPORTED"):
         P.pmcmc_solve_batched([d], P.Options(jac="dense", precision="f32"))
+
+
+def test_batched_with_basis_matches_oracle():
+    chains = _chains(SPEC, seed=11)
+    descs = []
+    for desc, ref, margin in chains:
+        t = desc.target
+        if t.kind == "gaussian":
+            _, Q = np.linalg.eigh(t.prec.cpu().double().numpy())
+        elif t.kind == "logreg":
+            X = t.X.cpu().double().numpy()
+            _, Q = np.linalg.eigh(X.T @ X)
+        else:
+            Q = None
+        if Q is not None:
+            t = P.Target(t.kind, t.D, mean=t.mean, prec=t.prec, X=t.X, y=t.y,
+                         prior_scale=t.prior_scale, Q=cu(Q))
+        descs.append(P.ChainDesc(t, desc.sampler, desc.step, desc.leapfrog_L, desc.T, desc.s0,
+                                 desc.xi, desc.u, desc.s_out))
+    opt = P.Options(jac="diag", precision="f32", atol=1e-6, rtol=1e-6, clip=1)
+    res = P.pmcmc_solve_batched(descs, opt)
+    for (_, ref, margin), d, r in zip(chains, descs, res):
+        assert r["status"] == "OK", (d.sampler, d.target.kind, d.target.D, r)
+        _check(d, ref, margin)

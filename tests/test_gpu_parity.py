@@ -449,3 +449,48 @@ def test_device_loop_and_host_loop_agree(kind):
     assert r1["iters"] == r2["iters"] and r1["status"] == r2["status"] == "OK"
     assert torch.equal(s1, s2)
     assert prof["eval_launches"] == r2["iters"] + 1 and prof["scan_launches"] == r2["iters"]
+
+
+# ------------------------------------------------------------------------------------------
+# orthogonal reparameterisation (Section 3.4)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("sampler", ["mala", "hmc"])
+def test_basis_reparam_gaussian_same_chain_fewer_iterations(dt, sampler):
+    """With Q the eigenvectors of P the rotated chain is the same chain (noise rotated with it)
+    and the diagonal Jacobian of Q^T J Q is exact for the linear part: far fewer iterations."""
+    D, T = 8, 1500
+    ot, gt = gauss_pair(D, seed=12, dt=dt)
+    lam, Q = np.linalg.eigh(ot.P)
+    eps = 0.5 / lam.max() if sampler == "mala" else 0.2 / np.sqrt(lam.max())
+    L = 5 if sampler == "hmc" else 0
+    xi, u = noise(T, D, 13, dt)
+    ref, ell, acc = O.chain(O.Problem(ot, sampler, eps, xi=xi, u=u, L=L), T, np.zeros(D))
+    margin = np.abs(np.minimum(ell, 0) - np.log(u))
+    atol = 1e-11 if dt == torch.float64 else 1e-6
+    opt = P.Options(sampler=sampler, step=eps, leapfrog_L=L, jac="diag", atol=atol,
+                    precision="f64" if dt == torch.float64 else "f32")
+    s_plain, r_plain = P.pmcmc_solve(gt, opt, T, cu(np.zeros(D), dt), xi=cu(xi, dt), u=cu(u))
+    gq = P.Target("gaussian", D, mean=gt.mean, prec=gt.prec, Q=cu(Q, dt))
+    s_q, r_q = P.pmcmc_solve(gq, opt, T, cu(np.zeros(D), dt), xi=cu(xi, dt), u=cu(u))
+    assert r_q["status"] == "OK"
+    _assert_trace(npy(s_q), ref, margin, dt)
+    assert r_q["iters"] < r_plain["iters"]
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_basis_reparam_logreg(dt):
+    ot, gt = logreg_pair(200, 12, seed=5, dt=dt)
+    _, V = np.linalg.eigh(ot.X.T @ ot.X)
+    T = 800
+    xi, u = noise(T, 12, 17, dt)
+    ref, ell, acc = O.chain(O.Problem(ot, "mala", 0.005, xi=xi, u=u), T, np.zeros(12))
+    margin = np.abs(np.minimum(ell, 0) - np.log(u))
+    gq = P.Target("logreg", 12, X=gt.X, y=gt.y, prior_scale=1.0, Q=cu(V, dt))
+    opt = P.Options(sampler="mala", step=0.005, jac="diag", clip=1,
+                    atol=1e-10 if dt == torch.float64 else 1e-6,
+                    precision="f64" if dt == torch.float64 else "f32")
+    s, r = P.pmcmc_solve(gq, opt, T, cu(np.zeros(12), dt), xi=cu(xi, dt), u=cu(u))
+    assert r["status"] == "OK"
+    _assert_trace(npy(s), ref, margin, dt)
