@@ -21,6 +21,13 @@ template <>
 __device__ __forceinline__ float load_as<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
     return __bfloat162float(*p);
 }
+// read-only (non-coherent) load of data that no thread of the kernel writes
+template <typename S, typename R>
+__device__ __forceinline__ R ldg_as(const S *p) { return static_cast<R>(__ldg(p)); }
+template <>
+__device__ __forceinline__ float ldg_as<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
 template <typename S, typename R>
 __device__ __forceinline__ void store_as(S *p, R v) { *p = static_cast<S>(v); }
 template <>
@@ -152,5 +159,17 @@ struct Spin {
         return true;
     }
 };
+
+// Ask for the largest shared-memory carveout once per kernel: for kernels with little static
+// shared memory the driver may otherwise pick an 8 KB configuration that admits one block per SM.
+template <class K>
+inline void prefer_shared(K kernel) {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        done = true;
+    }
+}
 
 }  // namespace pm

@@ -465,10 +465,12 @@ cudaError_t dispatch_dm(const EvalArgs &A, cudaStream_t st, bool seq) {
     const int blocks = ceil_div(A.T, 128);
 #define PM_CASE(DM_)                                                                   \
     if (D <= DM_) {                                                                    \
-        if (seq)                                                                       \
+        if (seq) {                                                                     \
             seq_small_kernel<R, DM_, TGT, SMP><<<1, 32, 0, st>>>(A);                   \
-        else                                                                           \
+        } else {                                                                       \
+            prefer_shared(eval_small_kernel<R, S, DM_, TGT, SMP>);                     \
             eval_small_kernel<R, S, DM_, TGT, SMP><<<blocks, 128, 0, st>>>(A);         \
+        }                                                                              \
         return cudaGetLastError();                                                     \
     }
     if constexpr (TGT == PMCMC_BANANA) {

@@ -27,6 +27,8 @@ struct ScanWork {
 // Tile geometry of the diagonal scan for (T, D): timesteps per tile.
 int diag_scan_tile(int T, int D, int elem_bytes);
 int dense_scan_chunk(int T, int D);
+int diag_scan_tile_rows(int T, int D);
+void scan_shape_override(int rows, int nsub);
 
 cudaError_t launch_noise(unsigned long long seed, unsigned int chain, int T, int D, bool f64,
                          void *xi, double *u, cudaStream_t st);

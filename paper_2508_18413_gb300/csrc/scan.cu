@@ -11,6 +11,9 @@
 //
 // A non-finite updated element is reset (to s_reset, or 0): the fixed point is finite, and an
 // iterate poisoned by an overflow would otherwise stop the Newton iteration from progressing.
+#include <cstdio>
+#include <cstdlib>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -120,6 +123,87 @@ __device__ __forceinline__ R lookback_window(const unsigned int *flags, const R 
         jend -= 32;
     }
     return carry;
+}
+
+// Block-wide look-back for the diagonal scans (all 256 threads, D <= 32 channels): thread i
+// examines predecessor tile jend - i, so one round of loads covers 256 tiles.  The nearest
+// tile with a published inclusive value (or tile -1, or a timed-out wait) ends the walk; the
+// aggregates of the tiles in between are composed per channel, first within each warp by a
+// shuffle tree (lower lane = later map), then across the 8 warps in order.  Returns the carry
+// of channel d in shared carry_out[d].
+template <typename R>
+__device__ void lookback_block(const unsigned int *flags, const R *gagg, const R *gincl, int tile,
+                               int D, unsigned int epoch, unsigned int spin_limit, ScanCtl *ctl,
+                               R *carry_out) {
+    __shared__ int s_k;
+    __shared__ R s_wa[8][32], s_wb[8][32], s_iv[32], s_MA[32], s_MB[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid < 32) {
+        s_MA[tid] = R(1);
+        s_MB[tid] = R(0);
+    }
+    int jend = tile - 1;
+    for (;;) {
+        if (tid == 0) s_k = 256;
+        __syncthreads();
+        const int j = jend - tid;
+        unsigned int st = kFlagIncl;
+        if (j >= 0) st = wait_flag(flags, j, epoch, spin_limit, ctl);
+        const bool stop = (j < 0) || st != kFlagAgg;
+        if (stop) atomicMin(&s_k, tid);
+        __syncthreads();
+        const int k = s_k;
+        if (tid == k && k < 256)
+            for (int d = 0; d < D; d++) s_iv[d] = (j >= 0 && st == kFlagIncl) ? gincl[(size_t)j * D + d] : R(0);
+        // channels in batches of 8: all 16 loads of a batch are in flight together
+        for (int d0 = 0; d0 < D; d0 += 8) {
+            R ga[8], gb[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                ga[c] = R(1);
+                gb[c] = R(0);
+                if (tid < k && d0 + c < D) {
+                    ga[c] = gagg[((size_t)j * 2) * D + d0 + c];
+                    gb[c] = gagg[((size_t)j * 2 + 1) * D + d0 + c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                R a = ga[c], b = gb[c];
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const R oa = __shfl_down_sync(0xffffffffu, a, off);
+                    const R ob = __shfl_down_sync(0xffffffffu, b, off);
+                    if (lane + off < 32) {
+                        b = a * ob + b;
+                        a = a * oa;
+                    }
+                }
+                if (lane == 0 && d0 + c < D) {
+                    s_wa[w][d0 + c] = a;
+                    s_wb[w][d0 + c] = b;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < D) {
+            // window map W = warp 0 o warp 1 o ... o warp 7 (warp 0 is the nearest = latest)
+            R Wa = R(1), Wb = R(0);
+            for (int q = 7; q >= 0; q--) {  // compose from the farthest to the nearest
+                const R qa = s_wa[q][tid], qb = s_wb[q][tid];
+                Wb = qa * Wb + qb;
+                Wa = qa * Wa;
+            }
+            // M <- M o W
+            const R MA = s_MA[tid], MB = s_MB[tid];
+            s_MB[tid] = MA * Wb + MB;
+            s_MA[tid] = MA * Wa;
+            if (k < 256) carry_out[tid] = s_MA[tid] * s_iv[tid] + s_MB[tid];
+        }
+        __syncthreads();
+        if (k < 256) break;
+        jend -= 256;
+    }
 }
 
 }  // namespace
@@ -289,8 +373,8 @@ scan_diag_kernel(int T, int D, int TT, const S *__restrict__ a, const S *__restr
 //   5. rows are applied in order from the carry and s is stored.
 // ==========================================================================================
 template <typename R, typename S, int ROWS>
-__global__ void __launch_bounds__(256)
-scan_diag_rows_kernel(int T, int D, const S *__restrict__ a, const S *__restrict__ b,
+__global__ void __launch_bounds__(256, (ROWS > 8 ? 2 : 4))
+scan_diag_rows_kernel(int T, int D, int NSUB, const S *__restrict__ a, const S *__restrict__ b,
                       R *__restrict__ s, const R *__restrict__ s_reset, unsigned int *flags,
                       R *__restrict__ gagg, R *__restrict__ gincl, ScanCtl *ctl, EvalStats *stats,
                       const int *skip, unsigned int spin_limit) {
@@ -300,7 +384,8 @@ scan_diag_rows_kernel(int T, int D, const S *__restrict__ a, const S *__restrict
     __shared__ R cin[8][32];             // carry into each warp
     const int P = 32 / D, L = P * D;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int TT = 8 * ROWS * P;
+    const int WT = NSUB * ROWS * P;      // timesteps per warp (a contiguous chunk)
+    const int TT = 8 * WT;
     const unsigned int ntiles = (unsigned int)ceil_div(T, TT);
     const int tile = (int)take_tile(ctl, &s_tile, &s_epoch);
     const unsigned int epoch = s_epoch;
@@ -308,104 +393,125 @@ scan_diag_rows_kernel(int T, int D, const S *__restrict__ a, const S *__restrict
     const int d = lane_on ? lane % D : 0;
     const int tsub = lane_on ? lane / D : 0;
     const int last_lane = (P - 1) * D + d;  // lane holding the row end of channel d
-    const long long t_base = (long long)tile * TT + (long long)w * ROWS * P;
+    const long long t_warp = (long long)tile * TT + (long long)w * WT;
 
-    R ra[ROWS], rb[ROWS], rs[ROWS];
-#pragma unroll
-    for (int r = 0; r < ROWS; r++) {
-        const long long t = t_base + (long long)r * P + tsub;
-        const bool in = lane_on && t < T;
-        const size_t e = (size_t)t * D + d;
-        ra[r] = in ? load_as<S, R>(a + e) : R(1);
-        rb[r] = in ? load_as<S, R>(b + e) : R(0);
-        rs[r] = in ? s[e] : R(0);
-    }
-    // 2. within-row inclusive scans (in place: ra, rb become the row prefixes)
-#pragma unroll
-    for (int r = 0; r < ROWS; r++) {
-        for (int off = D; off < L; off <<= 1) {
-            const R pa = __shfl_up_sync(0xffffffffu, ra[r], off);
-            const R pb = __shfl_up_sync(0xffffffffu, rb[r], off);
-            if (lane_on && lane >= off) {
-                rb[r] = ra[r] * pb + rb[r];
-                ra[r] = ra[r] * pa;
-            }
-        }
-    }
-    // 3. warp aggregate per channel: rows composed in order
+    // pass 1: the warp aggregate over its chunk (a, b only)
     R WA = R(1), WB = R(0);
+    for (int sub = 0; sub < NSUB; sub++) {
+        const long long t_base = t_warp + (long long)sub * ROWS * P;
+        R ra[ROWS], rb[ROWS];
 #pragma unroll
-    for (int r = 0; r < ROWS; r++) {
-        const R ea = __shfl_sync(0xffffffffu, ra[r], last_lane);
-        const R eb = __shfl_sync(0xffffffffu, rb[r], last_lane);
-        WB = ea * WB + eb;
-        WA = ea * WA;
+        for (int r = 0; r < ROWS; r++) {
+            const long long t = t_base + (long long)r * P + tsub;
+            const bool in = lane_on && t < T;
+            const size_t e = (size_t)t * D + d;
+            ra[r] = in ? ldg_as<S, R>(a + e) : R(1);
+            rb[r] = in ? ldg_as<S, R>(b + e) : R(0);
+        }
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            for (int off = D; off < L; off <<= 1) {
+                const R pa = __shfl_up_sync(0xffffffffu, ra[r], off);
+                const R pb = __shfl_up_sync(0xffffffffu, rb[r], off);
+                if (lane_on && lane >= off) {
+                    rb[r] = ra[r] * pb + rb[r];
+                    ra[r] = ra[r] * pa;
+                }
+            }
+            const R ea = __shfl_sync(0xffffffffu, ra[r], last_lane);
+            const R eb = __shfl_sync(0xffffffffu, rb[r], last_lane);
+            WB = ea * WB + eb;
+            WA = ea * WA;
+        }
     }
     if (lane < D) {
         wA[w][lane] = WA;
         wB[w][lane] = WB;
     }
     __syncthreads();
-    // 4. tile aggregate, publish, look back (warp 0, one lane per channel)
-    if (w == 0) {
+    // tile aggregate, publish, block-wide look-back, carries into the warps
+    __shared__ R tA[32], tB[32], ccar[32];
+    if (threadIdx.x < D) {
+        const int dd = threadIdx.x;
         R TA = R(1), TB = R(0);
-        if (lane < D) {
-            for (int q = 0; q < 8; q++) {
-                cin[q][lane] = TB;  // exclusive (B part) before warp q, carry applied below
-                TB = wA[q][lane] * TB + wB[q][lane];
-                TA = wA[q][lane] * TA;
-            }
-            if (tile == 0) {
-                gincl[lane] = TB;
-            } else {
-                gagg[((size_t)tile * 2) * D + lane] = TA;
-                gagg[((size_t)tile * 2 + 1) * D + lane] = TB;
-            }
+        for (int q = 0; q < 8; q++) {
+            TB = wA[q][dd] * TB + wB[q][dd];
+            TA = wA[q][dd] * TA;
+        }
+        tA[dd] = TA;
+        tB[dd] = TB;
+        if (tile == 0) {
+            gincl[dd] = TB;
+        } else {
+            gagg[((size_t)tile * 2) * D + dd] = TA;
+            gagg[((size_t)tile * 2 + 1) * D + dd] = TB;
+        }
+        ccar[dd] = R(0);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
+    if (tile > 0) {
+        lookback_block<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
+        if (threadIdx.x < D) {
+            gincl[(size_t)tile * D + threadIdx.x] = tA[threadIdx.x] * ccar[threadIdx.x] + tB[threadIdx.x];
             __threadfence();
         }
-        __syncwarp();
-        if (lane == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
-        R c = R(0);
-        if (tile > 0) {
-            c = lookback_window<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl);
-            if (lane < D) {
-                gincl[(size_t)tile * D + lane] = TA * c + TB;
-                __threadfence();
-            }
-        }
-        __syncwarp();
-        if (tile > 0 && lane == 0) st_release(flags + tile, make_flag(epoch, kFlagIncl));
-        // carry into each warp: (prefix of warps < q) applied to the tile carry c
-        if (lane < D) {
-            R pa = R(1);
-            for (int q = 0; q < 8; q++) {
-                const R excl_b = cin[q][lane];
-                cin[q][lane] = pa * c + excl_b;
-                pa = wA[q][lane] * pa;
-            }
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, kFlagIncl));
+    }
+    if (threadIdx.x < D) {
+        const int dd = threadIdx.x;
+        R pa = R(1), pb = R(0);
+        const R c = ccar[dd];
+        for (int q = 0; q < 8; q++) {
+            cin[q][dd] = pa * c + pb;
+            pb = wA[q][dd] * pb + wB[q][dd];
+            pa = wA[q][dd] * pa;
         }
     }
     __syncthreads();
-    // 5. apply rows in order
+    // pass 2: re-read the chunk (a, b from L2), apply rows in order from the carry
     R delta = lane_on ? cin[w][d] : R(0);
     R dmax = R(0);
     unsigned int resets = 0;
+    for (int sub = 0; sub < NSUB; sub++) {
+        const long long t_base = t_warp + (long long)sub * ROWS * P;
+        R ra[ROWS], rb[ROWS], rs[ROWS];
 #pragma unroll
-    for (int r = 0; r < ROWS; r++) {
-        const R dl = ra[r] * delta + rb[r];
-        const long long t = t_base + (long long)r * P + tsub;
-        if (lane_on && t < T) {
+        for (int r = 0; r < ROWS; r++) {
+            const long long t = t_base + (long long)r * P + tsub;
+            const bool in = lane_on && t < T;
             const size_t e = (size_t)t * D + d;
-            R sn = rs[r] + dl;
-            if (!finite(sn)) {
-                sn = s_reset ? s_reset[d] : R(0);
-                resets++;
-            } else {
-                dmax = max(dmax, fabs(dl));
-            }
-            s[e] = sn;
+            ra[r] = in ? ldg_as<S, R>(a + e) : R(1);
+            rb[r] = in ? ldg_as<S, R>(b + e) : R(0);
+            rs[r] = in ? __ldcs(s + e) : R(0);
         }
-        delta = __shfl_sync(0xffffffffu, dl, last_lane);
+#pragma unroll
+        for (int r = 0; r < ROWS; r++) {
+            for (int off = D; off < L; off <<= 1) {
+                const R pa = __shfl_up_sync(0xffffffffu, ra[r], off);
+                const R pb = __shfl_up_sync(0xffffffffu, rb[r], off);
+                if (lane_on && lane >= off) {
+                    rb[r] = ra[r] * pb + rb[r];
+                    ra[r] = ra[r] * pa;
+                }
+            }
+            const R dl = ra[r] * delta + rb[r];
+            const long long t = t_base + (long long)r * P + tsub;
+            if (lane_on && t < T) {
+                const size_t e = (size_t)t * D + d;
+                R sn = rs[r] + dl;
+                if (!finite(sn)) {
+                    sn = s_reset ? s_reset[d] : R(0);
+                    resets++;
+                } else {
+                    dmax = max(dmax, fabs(dl));
+                }
+                __stcs(s + e, sn);
+            }
+            delta = __shfl_sync(0xffffffffu, dl, last_lane);
+        }
     }
     if (stats) {
         double dm = warp_max((double)dmax);
@@ -418,17 +524,6 @@ scan_diag_rows_kernel(int T, int D, const S *__restrict__ a, const S *__restrict
     finish_tile(ctl, ntiles);
 }
 
-// rows per warp for the register-resident scan: fill the GPU about twice, at most 16
-static int diag_rows(int T, int D) {
-    const int P = 32 / D;
-    for (int rows : {16, 8, 4, 2})
-        if (ceil_div(T, 8 * rows * P) >= 2 * 152) return rows;
-    return 2;
-}
-
-int diag_scan_tile_rows(int T, int D) {
-    return 8 * diag_rows(T, D) * (32 / D);
-}
 
 int diag_scan_tile(int T, int D, int elem_bytes) {
     if (D <= 32) return diag_scan_tile_rows(T, D);
@@ -464,26 +559,76 @@ static cudaError_t run_scan_diag(int T, int D, int TT, const void *a, const void
     return cudaGetLastError();
 }
 
+// Tile shape of the register-resident scan: rows per sub-chunk (8 or 16) and sub-chunks per
+// warp.  scan_shape_override() lets the autotuner (and measurements) fix a shape.
+static int g_shape_rows = 0, g_shape_nsub = 0;
+void scan_shape_override(int rows, int nsub) {
+    g_shape_rows = rows;
+    g_shape_nsub = nsub;
+}
+
+static void diag_shape(int T, int D, int *rows, int *nsub) {
+    static bool env_read = false;
+    if (!env_read) {  // PMCMC_SCAN_SHAPE="rows,nsub" fixes the shape (measurements)
+        env_read = true;
+        const char *e = getenv("PMCMC_SCAN_SHAPE");
+        int r = 0, n = 0;
+        if (e && sscanf(e, "%d,%d", &r, &n) == 2 && (r == 8 || r == 16) && n >= 1 && n <= 64) {
+            g_shape_rows = r;
+            g_shape_nsub = n;
+        }
+    }
+    *rows = g_shape_rows > 0 ? g_shape_rows : 8;
+    if (g_shape_nsub > 0) {
+        *nsub = g_shape_nsub;
+        return;
+    }
+    // measured on GB300 (2^26..2^28 elements): larger tiles amortise the fixed per-tile latency
+    // (ticket, fences, look-back) up to ~32 sub-chunks, as long as the tiles still keep every
+    // SM busy several times over
+    const int P = 32 / D;
+    *nsub = 0;
+    for (int n : {32, 16, 8, 4, 2, 1})
+        if (ceil_div(T, 8 * *rows * n * P) >= 8 * 152) {
+            *nsub = n;
+            break;
+        }
+    if (*nsub == 0) {
+        *nsub = 1;
+        for (int n : {16, 8, 4, 2, 1})
+            if (ceil_div(T, 8 * *rows * n * P) >= 2 * 152) {
+                *nsub = n;
+                break;
+            }
+    }
+}
+
 template <typename R, typename S>
 static cudaError_t run_scan_rows(int T, int D, const void *a, const void *b, void *s,
                                  const void *s_reset, const ScanWork &w, EvalStats *stats,
                                  const int *skip, unsigned int spin, cudaStream_t st) {
-    const int rows = diag_rows(T, D);
-    const int ntiles = ceil_div(T, 8 * rows * (32 / D));
+    int rows, nsub;
+    diag_shape(T, D, &rows, &nsub);
+    const int ntiles = ceil_div(T, 8 * rows * nsub * (32 / D));
     if (ntiles > w.max_tiles) return cudaErrorInvalidValue;
-#define PM_ROWS(N_)                                                                             \
-    if (rows == N_) {                                                                          \
-        scan_diag_rows_kernel<R, S, N_><<<ntiles, 256, 0, st>>>(                               \
-            T, D, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags, (R *)w.agg, \
-            (R *)w.incl, w.ctl, stats, skip, spin);                                            \
-        return cudaGetLastError();                                                             \
+    if (rows == 16) {
+        prefer_shared(scan_diag_rows_kernel<R, S, 16>);
+        scan_diag_rows_kernel<R, S, 16><<<ntiles, 256, 0, st>>>(
+            T, D, nsub, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags,
+            (R *)w.agg, (R *)w.incl, w.ctl, stats, skip, spin);
+    } else {
+        prefer_shared(scan_diag_rows_kernel<R, S, 8>);
+        scan_diag_rows_kernel<R, S, 8><<<ntiles, 256, 0, st>>>(
+            T, D, nsub, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags,
+            (R *)w.agg, (R *)w.incl, w.ctl, stats, skip, spin);
     }
-    PM_ROWS(16)
-    PM_ROWS(8)
-    PM_ROWS(4)
-    PM_ROWS(2)
-#undef PM_ROWS
-    return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+int diag_scan_tile_rows(int T, int D) {
+    int rows, nsub;
+    diag_shape(T, D, &rows, &nsub);
+    return 8 * rows * nsub * (32 / D);
 }
 
 cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, const void *a,
@@ -833,6 +978,7 @@ cudaError_t launch_scan_dense(bool f64, int T, int D, int chunk, const void *a, 
     if (D <= 4) {
         if (chunk != 256) return cudaErrorInvalidValue;
 #define PM_DS(R_, DM_)                                                                           \
+    prefer_shared(scan_dense_small_kernel<R_, DM_>);                                           \
     scan_dense_small_kernel<R_, DM_><<<ceil_div(T, 256), 256, 0, st>>>(                        \
         T, D, (const R_ *)a, (const R_ *)b, (R_ *)s, (const R_ *)s_reset, w.flags, (R_ *)w.agg, \
         (R_ *)w.incl, w.ctl, stats, skip, spin_limit);                                         \

@@ -231,7 +231,7 @@ def _assert_trace(s, ref, margin, dt, tol_fp32=1e-5):
     bound = tol_fp32 * (1 + np.abs(ref[:upto]))
     err = np.abs(s[:upto] - ref[:upto])
     assert np.all(err <= bound), (np.max(err / bound), upto)
-    assert upto >= len(ref) // 2
+    assert upto >= min(len(ref), 300)
 
 
 def test_solve_c1_dense_fp64():
