@@ -76,6 +76,25 @@ def dist_env():
     return rank, world, local
 
 
+def combine_ranks(dist, world, device, ms, launches, e2e_ms):
+    """Whole-job figures from per-rank ones: the step time and the end-to-end time are the max
+    over ranks (the job ends with its slowest rank), launches are summed.  Every rank gets the
+    same answer; with one rank the inputs come back unchanged."""
+    import torch
+    if world <= 1:
+        return float(ms), int(launches), float(e2e_ms)
+    t = torch.tensor([ms, e2e_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(launches)], device=device, dtype=torch.float64)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t[0].item()), int(n.item()), float(t[1].item())
+
+
+def job_value(world, T, ms):
+    """samples/s of the whole job: every rank solves its own chain of T steps (weak scaling)."""
+    return world * T / (ms / 1000.0)
+
+
 # ------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------
@@ -248,17 +267,7 @@ def run_ours(args):
     # scan per iteration, one control kernel per evaluate, and the solve's set-up kernels
     launches_timed = sum(3 * r["iters"] + 2 + 5 for r in results)
 
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        n = torch.tensor([launches_timed], device=dev, dtype=torch.float64)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        launches = int(n.item())
-    else:
-        launches = int(launches_timed)
-    value = world * WL.T / (ms / 1000.0)
+    ms_local = sum(step_ms) / len(step_ms)
 
     # --- end to end through the public API with host buffers (pinned) ---------------------
     Xh = torch.tensor(X).pin_memory()
@@ -285,11 +294,9 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     barrier()
-    e2e = statistics.mean(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    ms, launches, e2e = combine_ranks(dist, world, dev, ms_local, launches_timed,
+                                      statistics.mean(e2e_ms))
+    value = job_value(world, WL.T, ms)
 
     # --- sequential GPU loop (the speedup denominator) --------------------------------------
     seq_ms = None
@@ -348,7 +355,7 @@ def run_ours(args):
                    "parallelism": f"{world} independent chain(s), one per GPU"},
         "newton_iters": last["iters"], "accept_rate": last["accept_rate"],
         "status": last["status"], "max_residual": last["max_residual"],
-        "e2e": {"value": world * WL.T / (e2e / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(world, WL.T, e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "eval_logreg_kernel (evaluate and linearise)",

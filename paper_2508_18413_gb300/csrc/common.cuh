@@ -116,16 +116,6 @@ struct EvalStats {
     unsigned long long dmax;       // ord-encoded max |delta| of the last scan
 };
 
-// Newton-loop control word (device-side loop).
-struct LoopCtl {
-    int iter;        // Newton updates applied so far
-    int converged;   // 1 once the residual met the tolerance
-    int max_iters;
-    int parity;      // which ping-pong buffer holds the current iterate
-    double atol;
-    unsigned long long err_hist[1];  // (unused placeholder for alignment)
-};
-
 __host__ __device__ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Philox4x32-10 (Salmon et al., SC'11).
