@@ -66,6 +66,11 @@ def parse():
                     help="solve in the eigenbasis of X^T X (Section 3.4 reparameterisation)")
     ap.add_argument("--gate-grad", type=int, default=0,
                     help="1: the stop-gradient gate term of Section 3.2 in J")
+    ap.add_argument("--scan-log2", default="20,22,24,26,28",
+                    help="scan_sweep: log2 of the element counts T*D")
+    ap.add_argument("--scan-d", type=int, default=8, help="scan_sweep: channels D")
+    ap.add_argument("--scan-precisions", default="f32,f32_scan_bf16",
+                    help="scan_sweep: precisions")
     return ap.parse_args()
 
 
@@ -527,11 +532,11 @@ def run_other(args):
     elif wl == "scan_sweep":
         rows = []
         peak = _measured_hbm()
-        for prec in ("f32", "f32_scan_bf16"):
-            for k in range(20, 29, 2):
-                n = 1 << k
-                D = 8
-                T = n // D
+        D = args.scan_d
+        for prec in args.scan_precisions.split(","):
+            for k in (int(x) for x in args.scan_log2.split(",")):
+                T = (1 << k) // D
+                n = T * D
                 sd = torch.float32
                 ad = torch.bfloat16 if prec == "f32_scan_bf16" else sd
                 a = (torch.rand((T, D), device=dev) * 1.8 - 0.9).to(ad)
@@ -544,7 +549,7 @@ def run_other(args):
                 rows.append({"precision": prec, "elements": n, "T": T, "D": D, "ms": ms,
                              "GB/s": gbs, "frac_of_measured_hbm": gbs / peak})
                 del a, b, sv
-        line.update(config="diagonal scan alone, a ~ U(-0.9, 0.9), b ~ N(0, 1), D = 8",
+        line.update(config=f"diagonal scan alone, a ~ U(-0.9, 0.9), b ~ N(0, 1), D = {D}",
                     unit="GB/s", rows=rows, hbm_peak_measured=peak)
     line["clocks"] = clocks.stop()
     print(json.dumps(line), flush=True)
