@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--scan-d", type=int, default=8, help="scan_sweep: channels D")
     ap.add_argument("--scan-precisions", default="f32,f32_scan_bf16",
                     help="scan_sweep: precisions")
+    ap.add_argument("--scan-kernel", choices=["rows", "staged"], default=None,
+                    help="diagonal scan kernel for D <= 32 (default: the library's choice)")
     return ap.parse_args()
 
 
@@ -564,6 +566,8 @@ def _measured_hbm():
 
 def main():
     args = parse()
+    if args.scan_kernel:
+        os.environ["PMCMC_SCAN_KERNEL"] = args.scan_kernel
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "c2":

@@ -110,6 +110,8 @@ typedef struct {
     unsigned long long seed; /* noise seed when xi/u are NULL, and for Hutchinson probes */
     unsigned int chain_id;   /* noise counter of this chain */
     int spin_limit;       /* look-back wait bound (polls); 0 = default */
+    int engine;           /* 0: automatic (tensor cores where a kernel exists: MALA on LOGREG,
+                             F32, D <= 32, DIAG with gate_grad 0 or ZERO); 1: CUDA cores only */
 } pmcmc_options;
 
 typedef struct {
@@ -123,7 +125,7 @@ typedef struct {
 } pmcmc_result;
 
 /* Fill `opt` with defaults: MALA, step 0.01, DIAG, F32, atol 1e-5, rtol 0, max_iters T,
- * damping 1, no clip, gate_grad 1, seed 0, chain 0. */
+ * damping 1, no clip, gate_grad 1, seed 0, chain 0, engine 0. */
 void pmcmc_options_default(pmcmc_options *opt);
 
 /* Create a context on CUDA device `device`.  Returns EINVAL/ECUDA on failure. */

@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib as L
-from ._lib import JACS, PRECISIONS, SAMPLERS, STATUS_NAMES, TARGETS
+from ._lib import ENGINES, JACS, PRECISIONS, SAMPLERS, STATUS_NAMES, TARGETS
 
 __all__ = [
     "PmcmcError", "Target", "Options", "pmcmc_create", "pmcmc_gen_noise", "pmcmc_solve",
@@ -117,13 +117,15 @@ class Options:
     seed: int = 0
     chain_id: int = 0
     spin_limit: int = 0
+    engine: str = "auto"   # "auto": tensor cores where a kernel exists; "simt": CUDA cores only
 
     def c(self) -> L.pmcmc_options:
         return L.pmcmc_options(SAMPLERS[self.sampler], float(self.step), int(self.leapfrog_L),
                                JACS[self.jac], PRECISIONS[self.precision], float(self.atol),
                                float(self.rtol), int(self.max_iters), float(self.damping),
                                int(self.clip), int(self.gate_grad), int(self.seed),
-                               int(self.chain_id), int(self.spin_limit))
+                               int(self.chain_id), int(self.spin_limit),
+                               ENGINES[self.engine])
 
 
 def _result_dict(r: L.pmcmc_result) -> dict:

@@ -17,6 +17,7 @@ SAMPLERS = {"mala": 0, "hmc": 1, "hmc_par_leapfrog": 2}
 TARGETS = {"gaussian": 0, "logreg": 1, "banana": 2}
 JACS = {"dense": 0, "diag": 1, "block2": 2, "diag_hutch": 3, "zero": 4}
 PRECISIONS = {"f64": 0, "f32": 1, "f32_scan_bf16": 2}
+ENGINES = {"auto": 0, "simt": 1}
 
 
 class pmcmc_target(C.Structure):
@@ -30,7 +31,8 @@ class pmcmc_options(C.Structure):
                 ("jac", C.c_int), ("precision", C.c_int), ("atol", C.c_double),
                 ("rtol", C.c_double), ("max_iters", C.c_int), ("damping", C.c_double),
                 ("clip", C.c_int), ("gate_grad", C.c_int), ("seed", C.c_ulonglong),
-                ("chain_id", C.c_uint), ("spin_limit", C.c_int)]
+                ("chain_id", C.c_uint), ("spin_limit", C.c_int),
+                ("engine", C.c_int)]
 
 
 class pmcmc_result(C.Structure):

@@ -152,14 +152,40 @@ struct Spin {
 
 // Ask for the largest shared-memory carveout once per kernel: for kernels with little static
 // shared memory the driver may otherwise pick an 8 KB configuration that admits one block per SM.
+// Keyed by the kernel's address: kernels of identical signature share a template instance.
 template <class K>
 inline void prefer_shared(K kernel) {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-        done = true;
+    static const void *done[32] = {};
+    static int n = 0;
+    const void *key = reinterpret_cast<const void *>(kernel);
+    for (int i = 0; i < n; i++)
+        if (done[i] == key) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    if (n < 32) done[n++] = key;
+}
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (cached per kernel).  Static
+// plus dynamic shared memory above 48 KB needs this opt-in, so it is applied to every size.
+template <class K>
+inline cudaError_t ensure_dyn_smem(K kernel, size_t bytes) {
+    static const void *keys[32] = {};
+    static size_t vals[32] = {};
+    static int n = 0;
+    const void *key = reinterpret_cast<const void *>(kernel);
+    int i = 0;
+    for (; i < n; i++)
+        if (keys[i] == key) break;
+    if (i < n && vals[i] >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (i < n) {
+        vals[i] = bytes;
+    } else if (n < 32) {
+        keys[n] = key;
+        vals[n++] = bytes;
     }
+    return cudaSuccess;
 }
 
 }  // namespace pm

@@ -48,6 +48,11 @@ struct EvalArgs {
     unsigned int chain = 0;
     const int *iter = nullptr;  // device Newton iteration counter (Hutchinson probes)
     const int *skip = nullptr;  // device flag: skip the launch when set (device-side loop)
+    // tensor-core path (logistic MALA, D <= 32)
+    int engine = 0;                   // pmcmc_options.engine: 0 automatic, 1 CUDA cores only
+    const void *tc_img = nullptr;     // chunk images of the design (launch_logreg_tc_pack)
+    unsigned int *timeout = nullptr;  // set to 1 when a bounded wait ran out
+    unsigned int spin_limit = 0;      // polls per wait; 0 = default
 };
 
 cudaError_t launch_eval_small(const EvalArgs &A, cudaStream_t st);
@@ -56,5 +61,11 @@ cudaError_t launch_eval_logreg(const EvalArgs &A, cudaStream_t st);
 cudaError_t launch_seq_logreg(const EvalArgs &A, cudaStream_t st);
 cudaError_t launch_logreg_dense_jac(const EvalArgs &A, cudaStream_t st);
 int logreg_padded_dim(int D);
+
+// tensor-core evaluate-and-linearise of logistic MALA (eval_logreg_tc.cu)
+bool logreg_tc_supported(const EvalArgs &A);
+size_t logreg_tc_image_bytes(int N);
+cudaError_t launch_logreg_tc_pack(const void *X, const void *y, int N, int D, void *img, cudaStream_t st);
+cudaError_t launch_eval_logreg_tc(const EvalArgs &A, cudaStream_t st);
 
 }  // namespace pm

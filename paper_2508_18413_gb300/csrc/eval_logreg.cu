@@ -444,6 +444,7 @@ static cudaError_t run_eval_logreg(const EvalArgs &A, cudaStream_t st) {
 }
 
 cudaError_t launch_eval_logreg(const EvalArgs &A, cudaStream_t st) {
+    if (A.tc_img && logreg_tc_supported(A)) return launch_eval_logreg_tc(A, st);
     const int DP = logreg_padded_dim(A.D);
 #define PM_LR(R_, S_)                                                   \
     switch (DP) {                                                       \

@@ -1,0 +1,525 @@
+// Evaluate-and-linearise pass of MALA on Bayesian logistic regression (Section 5.2 target) on
+// the fifth-generation tensor cores: tcgen05.mma of kind::tf32 with FP32 accumulators in
+// tensor memory (TMEM).  Covers D <= 32, FP32 arithmetic, the exact diagonal of the held-gate
+// Jacobian (Section 3.2 with the gate value held) or the zero Jacobian.
+//
+// Per timestep t a MALA linearisation needs, with x = s_{t-1} and x~ the proposal,
+//   z = X x,  g(x) = X^T (y - sigmoid(z)) - x / sp^2,  sum_n [y z - softplus(z)],
+//   diag(X^T W X), W = diag(sigmoid'(z))           (pass 1, at x)
+//   the same gradient and log-likelihood at x~     (pass 2)
+// For a CTA of 128 timesteps the contractions are GEMMs against the shared design matrix:
+//   Z = V X^T (128 x N),  G = C X (128 x D),  H = W (X.X) (128 x D),
+// computed in chunks of 32 design rows.  Each FP32 operand is split a = a_hi + a_lo into two
+// tf32 values and a b is accumulated as a_lo b_hi + a_hi b_lo + a_hi b_hi (the dropped
+// a_lo b_lo term is below 2^-22 |a b|); the diagonal Hessian H only shapes the Newton step and
+// takes the single product a_hi b_hi.
+//
+// Warp roles (576 threads, one CTA per SM):
+//   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one timestep per lane) and
+//              belongs to warpgroup h = w / 4, which owns columns 8h..8h+7 of every chunk and
+//              dimensions 8h..8h+7 of the state.  Z -> c = y - sigmoid(z), w = sigmoid'(z) and
+//              the log-likelihood terms; c, w are written as tf32 pairs into shared memory as
+//              the A operand of G and H.  Each warpgroup forms its dimensions of the proposal,
+//              of the residual and of J; the MH log-ratio (FP64) is summed over the four
+//              warpgroups through shared memory.
+//   warp 16    allocates TMEM and issues every MMA from one thread.
+//   warp 17    one thread streams pre-swizzled design chunks with bulk copies (3 stages).
+// TMEM: Z double buffered (columns 0-31, 32-63); G per chunk, double buffered (64-95, 96-127);
+// H accumulated over the chunks (128-159).  The tensor core's FP32 accumulation truncates, so
+// a sum over all N rows in one accumulator would drift by up to an ulp of |G| per MMA; each
+// chunk's G product therefore starts a fresh accumulator and the epilogue adds the 32-row
+// partials in registers with round-to-nearest.  Every wait is bounded: a wait that runs out
+// raises the CTA's abort flag, the roles finish without further work, in-flight copies and
+// MMAs are drained, TMEM is freed and the launch's timeout word is set.
+#include "common.cuh"
+#include "eval.h"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace pm {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kM = 128;                        // timesteps per CTA (MMA M; one TMEM lane each)
+constexpr int kNB = 32;                        // design rows per chunk
+constexpr int kDP = 32;                        // padded feature dimension
+constexpr int kStages = 3;                     // chunk images in flight
+constexpr int kGroups = 4;                     // epilogue warpgroups
+constexpr int kCols = kDP / kGroups;           // columns / dimensions per warpgroup: 8
+constexpr int kEpiWarps = 4 * kGroups;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = kEpiThreads + 64;     // + MMA warp + copy warp
+constexpr int kMmaWarp = kEpiWarps, kCopyWarp = kEpiWarps + 1;
+constexpr int kOp = kNB * kDP * 4;             // one 32 x 32 operand block: 4096 bytes
+constexpr int kImg = 5 * kOp + kNB * 4;        // chunk image: X hi, X lo, X^T hi, X^T lo, (X.X)^T hi, y
+constexpr int kStageStride = 21504;            // 1024-aligned stage slot
+constexpr int kRowOp = kM * kDP * 4;           // a 128 x 32 A operand: 16384 bytes
+constexpr uint32_t kIdesc = idesc_tf32(kM, 32);
+constexpr uint32_t kTmemCols = 256;
+constexpr unsigned int kDrainLimit = 1u << 22;
+
+// shared-memory map, offsets from a 1024-aligned base
+constexpr int oVhi = 0, oVlo = kRowOp;         // A operand of Z: the states (x, then x~)
+constexpr int oCW = 2 * kRowOp;                // 2 buffers of (C hi, C lo, W hi)
+constexpr int kCWStride = 3 * kRowOp;
+constexpr int oStage = oCW + 2 * kCWStride;
+constexpr int oBar = oStage + kStages * kStageStride;
+constexpr int bFull = 0, bEmpty = kStages, bZfull = 2 * kStages, bCfull = bZfull + 2,
+              bCempty = bCfull + 2, bGdone = bCempty + 2, bVready = bGdone + 1, bFin = bVready + 1,
+              kNumBars = bFin + 1;
+constexpr int oMisc = oBar + 8 * kNumBars;     // tmem address, abort flag
+constexpr int oPart = oMisc + 16;              // double [4][128]: per-warpgroup log-ratio parts
+constexpr int oAcc = oPart + kGroups * kM * 8; // int [128]: decisions
+constexpr int oRed = oAcc + kM * 4;            // double [16][4]: per-warp statistics
+constexpr int kSmemUsed = oRed + kEpiWarps * 4 * 8;
+constexpr int kSmemBytes = kSmemUsed + 1024;   // + alignment slack
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+static_assert(oStage % 1024 == 0 && kStageStride % 1024 == 0 && oCW % 1024 == 0, "alignment");
+
+__device__ __forceinline__ float post_jac(float v, float damping, int clip) {
+    v *= damping;
+    if (clip) v = fminf(fmaxf(v, -1.0f), 1.0f);
+    return v;
+}
+
+// write columns 8h..8h+7 of row r of a 128 x 32 K-major swizzled operand as a tf32 pair
+__device__ __forceinline__ void put_row_pair(unsigned char *hi, unsigned char *lo, int r, int h,
+                                             const float (&v)[kCols]) {
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        float h4[4], l4[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            h4[e] = to_tf32(v[4 * c + e]);
+            l4[e] = to_tf32(v[4 * c + e] - h4[e]);
+        }
+        const uint32_t off = swz128((uint32_t)r, (uint32_t)(kCols * h + 4 * c));
+        *reinterpret_cast<float4 *>(hi + off) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+        *reinterpret_cast<float4 *>(lo + off) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+    }
+}
+
+// warp-uniform bounded wait (every lane takes the same branch afterwards)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort,
+                                          unsigned int limit) {
+    const bool ok = mbar_wait(bar, parity, abort, limit);
+    return __all_sync(0xffffffffu, ok);
+}
+
+template <typename S_>
+__global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A) {
+    if (A.skip && *(volatile const int *)A.skip) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const uint32_t sb = smem_u32(sm);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int T = A.T, D = A.D, N = A.N;
+    const int t0 = blockIdx.x * kM;
+    const int nch = (N + kNB - 1) / kNB;
+    const bool want_dh = A.jac == PMCMC_JAC_DIAG;
+    const unsigned int limit = A.spin_limit ? A.spin_limit : kDefaultSpinLimit;
+    volatile int *abort_f = reinterpret_cast<volatile int *>(sm + oMisc + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + oMisc);
+    auto bar = [&](int i) -> uint32_t { return sb + oBar + 8u * (uint32_t)i; };
+
+    if (tid == 0) {
+        for (int i = 0; i < kNumBars; i++) {
+            uint32_t cnt = 1;
+            if (i == bCfull || i == bCfull + 1 || i == bVready) cnt = kEpiThreads;
+            mbar_init(bar(i), cnt);
+        }
+        *abort_f = 0;
+        fence_barrier_init();
+    }
+    if (warp == kMmaWarp) {
+        tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = *tmem_slot;
+
+    if (warp == kCopyWarp) {
+        // ---------------- producer: chunk images, both passes ----------------
+        if (lane == 0) {
+            const unsigned char *img = static_cast<const unsigned char *>(A.tc_img);
+            int k = 0;
+            for (; k < 2 * nch; k++) {
+                const int s = k % kStages;
+                if (k >= kStages && !mbar_wait(bar(bEmpty + s), (uint32_t)((k / kStages) - 1) & 1u, abort_f, limit))
+                    break;
+                mbar_arrive_expect_tx(bar(bFull + s), kImg);
+                bulk_g2s(sb + oStage + s * kStageStride, img + (size_t)(k % nch) * kImg, kImg, bar(bFull + s));
+            }
+            for (int q = k > kStages ? k - kStages : 0; q < k; q++)
+                mbar_wait_drain(bar(bFull + q % kStages), (uint32_t)(q / kStages) & 1u, kDrainLimit);
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issue (one thread) ----------------
+        if (lane == 0) {
+            auto issue_z = [&](int k) -> bool {
+                const int s = k % kStages;
+                if (!mbar_wait(bar(bFull + s), (uint32_t)(k / kStages) & 1u, abort_f, limit)) return false;
+                tc_fence_after();
+                const uint32_t st = sb + oStage + s * kStageStride;
+                const uint32_t zt = tm + (uint32_t)(k & 1) * 32u;
+#pragma unroll
+                for (int kk = 0; kk < 4; kk++) {
+                    const uint64_t ah = sdesc(sb + oVhi + 32 * kk), al = sdesc(sb + oVlo + 32 * kk);
+                    const uint64_t bh = sdesc(st + 32 * kk), bl = sdesc(st + kOp + 32 * kk);
+                    mma_tf32(zt, al, bh, kIdesc, kk > 0);
+                    mma_tf32(zt, ah, bl, kIdesc, 1);
+                    mma_tf32(zt, ah, bh, kIdesc, 1);
+                }
+                mma_commit(bar(bZfull + (k & 1)));
+                return true;
+            };
+            bool ok = true;
+            for (int pass = 0; pass < 2 && ok; pass++) {
+                ok = mbar_wait(bar(bVready), (uint32_t)pass, abort_f, limit);
+                if (!ok) break;
+                tc_fence_after();
+                const int kb = pass * nch;
+                ok = issue_z(kb);
+                for (int j = 0; j < nch && ok; j++) {
+                    const int k = kb + j;
+                    if (j + 1 < nch && !(ok = issue_z(k + 1))) break;
+                    if (!(ok = mbar_wait(bar(bCfull + (k & 1)), (uint32_t)(k >> 1) & 1u, abort_f, limit))) break;
+                    tc_fence_after();
+                    const uint32_t st = sb + oStage + (k % kStages) * kStageStride;
+                    const uint32_t cw = sb + oCW + (k & 1) * kCWStride;
+                    const uint32_t gt = tm + 64 + (uint32_t)(k & 1) * 32u;  // fresh per chunk
+#pragma unroll
+                    for (int kk = 0; kk < 4; kk++) {
+                        const uint64_t ch = sdesc(cw + 32 * kk), cl = sdesc(cw + kRowOp + 32 * kk);
+                        const uint64_t bh = sdesc(st + 2 * kOp + 32 * kk), bl = sdesc(st + 3 * kOp + 32 * kk);
+                        mma_tf32(gt, cl, bh, kIdesc, kk > 0 ? 1u : 0u);
+                        mma_tf32(gt, ch, bl, kIdesc, 1);
+                        mma_tf32(gt, ch, bh, kIdesc, 1);
+                    }
+                    if (pass == 0 && want_dh) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; kk++)
+                            mma_tf32(tm + 128, sdesc(cw + 2 * kRowOp + 32 * kk), sdesc(st + 4 * kOp + 32 * kk),
+                                     kIdesc, (j > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(bar(bCempty + (k & 1)));
+                    mma_commit(bar(bEmpty + k % kStages));
+                }
+                if (ok) mma_commit(bar(bGdone));
+            }
+            mma_commit(bar(bFin));
+            mbar_wait_drain(bar(bFin), 0, kDrainLimit);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warpgroups ----------------
+        const int q = warp & 3, h = warp >> 2;
+        const int r = q * 32 + lane;
+        const int t = t0 + r;
+        const bool tv = t < T;
+        const int d0 = kCols * h;  // this warpgroup's dimensions d0 .. d0 + 7
+        const uint32_t lrow = tm + ((uint32_t)(q * 32) << 16);
+        const float eps = (float)A.eps;
+        const float inv_sp2 = (float)(1.0 / (A.sigma_p * A.sigma_p));
+        const float *s = static_cast<const float *>(A.s);
+        const float *s0 = static_cast<const float *>(A.s0);
+        const float *xin = static_cast<const float *>(A.xi);
+        // own dimensions of x = s_{t-1} and of the noise, re-read where needed (L2)
+        auto load_x = [&](float (&v)[kCols]) {
+#pragma unroll
+            for (int i = 0; i < kCols; i++) {
+                const int d = d0 + i;
+                v[i] = (tv && d < D) ? (t == 0 ? s0[d] : s[(size_t)(t - 1) * D + d]) : 0.0f;
+            }
+        };
+        auto load_xi = [&](float (&v)[kCols]) {
+#pragma unroll
+            for (int i = 0; i < kCols; i++) {
+                const int d = d0 + i;
+                v[i] = (tv && d < D) ? xin[(size_t)t * D + d] : 0.0f;
+            }
+        };
+        float xt[kCols];              // the proposal (own dimensions)
+        float gs[kCols];              // running G sum (own dimensions)
+        double ll0 = 0.0, ll1 = 0.0;  // log-likelihood partials (own columns) of the two passes
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < kCols; i++) xt[i] = gs[i] = 0.0f;
+        {
+            float x[kCols];
+            load_x(x);
+            put_row_pair(sm + oVhi, sm + oVlo, r, h, x);
+            fence_async_smem();
+            mbar_arrive(bar(bVready));
+        }
+        auto add_partial = [&](int kc) {  // G of chunk kc, own dimensions
+            float gp[kCols];
+            tmem_ld8(lrow + 64 + 32u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < kCols; i++) gs[i] += gp[i];
+        };
+        for (int pass = 0; pass < 2; pass++) {
+            for (int j = 0; j < nch && ok; j++) {
+                const int k = pass * nch + j, b = k & 1, si = k % kStages;
+                if (!(ok = warp_wait(bar(bZfull + b), (uint32_t)(k >> 1) & 1u, abort_f, limit))) break;
+                if (!(ok = warp_wait(bar(bFull + si), (uint32_t)(k / kStages) & 1u, abort_f, limit))) break;
+                tc_fence_after();
+                float z[kCols];
+                tmem_ld8(lrow + (uint32_t)b * 32u + (uint32_t)d0, z);
+                const float4 *ys4 = reinterpret_cast<const float4 *>(sm + oStage + si * kStageStride + 5 * kOp) + 2 * h;
+                const float4 ya = ys4[0], yb = ys4[1];
+                const float yv8[kCols] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                tmem_wait_ld();
+                float chi[kCols], clo[kCols], whi[kCols];
+                float llc = 0.0f;
+                const int nbase = j * kNB + d0;
+                const bool full = nbase + kCols <= N;
+#pragma unroll
+                for (int i = 0; i < kCols; i++) {
+                    const float zz = z[i];
+                    const float yv = yv8[i];
+                    const float m = __expf(-fabsf(zz));
+                    const float qv = __fdividef(1.0f, 1.0f + m);
+                    const float mq = m * qv;
+                    const float p = zz >= 0.0f ? qv : mq;   // sigmoid(z)
+                    const float pc = zz >= 0.0f ? mq : qv;  // 1 - sigmoid(z)
+                    float c = yv - p;
+                    float w = p * pc;
+                    float ln = yv * zz - (fmaxf(zz, 0.0f) + __logf(1.0f + m));  // y z - softplus(z)
+                    if (!full && nbase + i >= N) {
+                        c = 0.0f;
+                        w = 0.0f;
+                        ln = 0.0f;
+                    }
+                    llc += ln;
+                    chi[i] = to_tf32(c);
+                    clo[i] = to_tf32(c - chi[i]);
+                    whi[i] = to_tf32(w);
+                }
+                if (pass) ll1 += (double)llc;
+                else ll0 += (double)llc;
+                if (k >= 2) {
+                    // G of chunk k - 2 is complete: its C buffer is free and its partial readable
+                    if (!(ok = warp_wait(bar(bCempty + b), (uint32_t)((k - 2) >> 1) & 1u, abort_f, limit))) break;
+                    tc_fence_after();
+                    if (j >= 2) add_partial(k - 2);
+                }
+                unsigned char *cw = sm + oCW + b * kCWStride;
+#pragma unroll
+                for (int c4 = 0; c4 < 2; c4++) {
+                    const uint32_t off = swz128((uint32_t)r, (uint32_t)(d0 + 4 * c4));
+                    *reinterpret_cast<float4 *>(cw + off) =
+                        make_float4(chi[4 * c4], chi[4 * c4 + 1], chi[4 * c4 + 2], chi[4 * c4 + 3]);
+                    *reinterpret_cast<float4 *>(cw + kRowOp + off) =
+                        make_float4(clo[4 * c4], clo[4 * c4 + 1], clo[4 * c4 + 2], clo[4 * c4 + 3]);
+                    if (pass == 0 && want_dh)
+                        *reinterpret_cast<float4 *>(cw + 2 * kRowOp + off) =
+                            make_float4(whi[4 * c4], whi[4 * c4 + 1], whi[4 * c4 + 2], whi[4 * c4 + 3]);
+                }
+                fence_async_smem();
+                tc_fence_before();
+                mbar_arrive(bar(bCfull + b));
+            }
+            // pass end: the last one or two partials complete G of this pass
+            if (ok && (ok = warp_wait(bar(bGdone), (uint32_t)pass, abort_f, limit))) {
+                tc_fence_after();
+                const int kb = pass * nch;
+                if (nch >= 2) add_partial(kb + nch - 2);
+                add_partial(kb + nch - 1);
+                if (pass == 0) {
+                    // the proposal x~ = x + eps grad log p(x) + sqrt(2 eps) xi (own dimensions)
+                    float x[kCols], xv[kCols];
+                    load_x(x);
+                    load_xi(xv);
+                    const float sq = sqrtf(2.0f * eps);
+#pragma unroll
+                    for (int i = 0; i < kCols; i++)
+                        xt[i] = d0 + i < D ? x[i] + eps * (gs[i] - x[i] * inv_sp2) + sq * xv[i] : 0.0f;
+                    put_row_pair(sm + oVhi, sm + oVlo, r, h, xt);
+                    fence_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(bar(bVready));
+#pragma unroll
+                    for (int i = 0; i < kCols; i++) gs[i] = 0.0f;
+                }
+            }
+        }
+        // gs holds the own dimensions of the G row at x~.  The MH log-ratio (FP64):
+        //   ell = [ll(x~) - |x~|^2/2sp2] - [ll(x) - |x|^2/2sp2] - |e|^2/(4 eps) + |xi|^2/2,
+        //   e = x - x~ - eps grad log p(x~), summed over the four warpgroups.
+        double *part = reinterpret_cast<double *>(sm + oPart);
+        int *accf = reinterpret_cast<int *>(sm + oAcc);
+        float x[kCols];
+        load_x(x);
+        {
+            float xv[kCols];
+            load_xi(xv);
+            const double sp2 = A.sigma_p * A.sigma_p;
+            double quad = ll1 - ll0;
+#pragma unroll
+            for (int i = 0; i < kCols; i++) {
+                if (d0 + i < D) {
+                    const float g2 = gs[i] - xt[i] * inv_sp2;
+                    const float e = x[i] - xt[i] - eps * g2;
+                    quad += -((double)xt[i] * xt[i] - (double)x[i] * x[i]) / (2.0 * sp2) -
+                            (double)e * e / (4.0 * (double)eps) + 0.5 * (double)xv[i] * xv[i];
+                }
+            }
+            part[h * kM + r] = quad;
+        }
+        named_bar(1, kEpiThreads);
+        const bool valid = tv && ok && !*abort_f;
+        double margin = INFINITY;
+        int acc_i = 0;
+        if (h == 0) {
+            int acc = 0;
+            if (valid) {
+                const double ell = part[r] + part[kM + r] + part[2 * kM + r] + part[3 * kM + r];
+                const double la = (ell < 0.0 || isnan(ell)) ? ell : 0.0;
+                const double gtl = la - log(A.u[t]);
+                acc = gtl > 0.0;
+                margin = fabs(gtl);
+                acc_i = acc;
+                if (A.ell_out) A.ell_out[t] = ell;
+                if (A.acc_out) A.acc_out[t] = acc ? 1 : 0;
+            }
+            accf[r] = acc;
+        }
+        named_bar(1, kEpiThreads);
+        double err = -INFINITY, rmax = 0.0;
+        float dh[kCols];
+#pragma unroll
+        for (int i = 0; i < kCols; i++) dh[i] = 0.0f;
+        if (want_dh && ok) {
+            // diag(X^T W X) accumulated over the chunks of pass 1 (untouched by pass 2); the
+            // condition is warp-uniform, as the collective TMEM load requires
+            tmem_ld8(lrow + 128 + (uint32_t)d0, dh);
+            tmem_wait_ld();
+        }
+        if (valid) {
+            const bool acc = accf[r] != 0;
+            S_ *bout = static_cast<S_ *>(A.b_out);
+            S_ *aout = static_cast<S_ *>(A.a_out);
+            float *fout = static_cast<float *>(A.f_out);
+            const float damping = (float)A.damping;
+#pragma unroll
+            for (int i = 0; i < kCols; i++) {
+                const int d = d0 + i;
+                if (d < D) {
+                    const size_t o = (size_t)t * D + d;
+                    const float f = acc ? xt[i] : x[i];
+                    const float sv = s[o];
+                    const float rr = f - sv;
+                    const double ar = fabs((double)rr);
+                    const double ee = ar - A.rtol * fabs((double)sv);
+                    err = isnan(ee) ? INFINITY : fmax(err, ee);
+                    rmax = isnan(ar) ? INFINITY : fmax(rmax, ar);
+                    if (bout) store_as<S_, float>(bout + o, rr);
+                    if (fout) fout[o] = f;
+                    if (aout) {
+                        float jv = 0.0f;
+                        if (want_dh) jv = post_jac(acc ? 1.0f + eps * (-dh[i] - inv_sp2) : 1.0f, damping, A.clip);
+                        store_as<S_, float>(aout + o, jv);
+                    }
+                }
+            }
+        }
+        if (A.stats) {
+            double *red = reinterpret_cast<double *>(sm + oRed);
+            const double e1 = warp_max(err), e2 = warp_max(rmax), e3 = warp_min(margin);
+            const double e4 = warp_sum((double)acc_i);
+            if (lane == 0) {
+                red[4 * warp + 0] = e1;
+                red[4 * warp + 1] = e2;
+                red[4 * warp + 2] = e3;
+                red[4 * warp + 3] = e4;
+            }
+            named_bar(1, kEpiThreads);
+            if (tid == 0) {
+                double m1 = red[0], m2 = red[1], m3 = red[2], m4 = red[3];
+                for (int w = 1; w < kEpiWarps; w++) {
+                    m1 = fmax(m1, red[4 * w]);
+                    m2 = fmax(m2, red[4 * w + 1]);
+                    m3 = fmin(m3, red[4 * w + 2]);
+                    m4 += red[4 * w + 3];
+                }
+                atomic_max_d(&A.stats->err, m1);
+                atomic_max_d(&A.stats->rmax, m2);
+                atomic_min_d(&A.stats->min_margin, m3);
+                if (m4 > 0) atomicAdd(&A.stats->accepts, (unsigned long long)(m4 + 0.5));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tm, kTmemCols);
+    }
+    if (tid == 0 && *abort_f && A.timeout) atomicExch(A.timeout, 1u);
+}
+
+// Chunk images of the design: per chunk of 32 rows, the tf32 pair of X (rows n, columns d),
+// the tf32 pair of X^T (rows d, columns n), tf32 of (X.X)^T, and the 32 labels; each operand
+// block already in the swizzled shared-memory layout, so one bulk copy stages a chunk.
+__global__ void logreg_tc_pack_kernel(const float *__restrict__ X, const float *__restrict__ y, int N, int D,
+                                      unsigned char *__restrict__ img) {
+    unsigned char *base = img + (size_t)blockIdx.x * kImg;
+    for (int e = threadIdx.x; e < kNB * kDP; e += blockDim.x) {
+        const int nl = e / kDP, d = e % kDP;
+        const int n = blockIdx.x * kNB + nl;
+        const float v = (n < N && d < D) ? X[(size_t)n * D + d] : 0.0f;
+        const float hi = to_tf32(v), lo = to_tf32(v - hi);
+        *reinterpret_cast<float *>(base + 0 * kOp + swz128(nl, d)) = hi;
+        *reinterpret_cast<float *>(base + 1 * kOp + swz128(nl, d)) = lo;
+        *reinterpret_cast<float *>(base + 2 * kOp + swz128(d, nl)) = hi;
+        *reinterpret_cast<float *>(base + 3 * kOp + swz128(d, nl)) = lo;
+        *reinterpret_cast<float *>(base + 4 * kOp + swz128(d, nl)) = to_tf32(v * v);
+    }
+    if (threadIdx.x < kNB) {
+        const int n = blockIdx.x * kNB + threadIdx.x;
+        reinterpret_cast<float *>(base + 5 * kOp)[threadIdx.x] = n < N ? y[n] : 0.0f;
+    }
+}
+
+}  // namespace
+
+bool logreg_tc_supported(const EvalArgs &A) {
+    return !A.f64 && A.engine == 0 && A.target == PMCMC_LOGREG && A.sampler == PMCMC_MALA && A.D >= 1 &&
+           A.D <= kDP && A.N >= 1 &&
+           (A.jac == PMCMC_JAC_ZERO || (A.jac == PMCMC_JAC_DIAG && A.gate_grad == 0));
+}
+
+size_t logreg_tc_image_bytes(int N) { return (size_t)ceil_div(N, kNB) * kImg; }
+
+cudaError_t launch_logreg_tc_pack(const void *X, const void *y, int N, int D, void *img, cudaStream_t st) {
+    if (N <= 0 || D > kDP) return cudaErrorInvalidValue;
+    logreg_tc_pack_kernel<<<ceil_div(N, kNB), 256, 0, st>>>(static_cast<const float *>(X),
+                                                           static_cast<const float *>(y), N, D,
+                                                           static_cast<unsigned char *>(img));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_logreg_tc(const EvalArgs &A, cudaStream_t st) {
+    if (!A.tc_img || reinterpret_cast<uintptr_t>(A.tc_img) % 16 != 0) return cudaErrorInvalidValue;
+    if (A.T <= 0) return cudaSuccess;
+    static bool attr_set[2] = {false, false};
+    const int which = A.bf16 ? 1 : 0;
+    auto k = A.bf16 ? eval_logreg_tc_kernel<__nv_bfloat16> : eval_logreg_tc_kernel<float>;
+    if (!attr_set[which]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set[which] = true;
+    }
+    k<<<ceil_div(A.T, kM), kThreads, kSmemBytes, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace pm

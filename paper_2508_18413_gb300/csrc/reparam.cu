@@ -60,11 +60,11 @@ cudaError_t rot_rows(void *dst, const void *src, const void *Q, long long rows, 
     if (grid < 1) grid = 1;
     if (f64) {
         auto k = rot_rows_kernel<double>;
-        if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        ensure_dyn_smem(k, sm);
         k<<<grid, 256, sm, st>>>((double *)dst, (const double *)src, (const double *)Q, rows, D, transpose);
     } else {
         auto k = rot_rows_kernel<float>;
-        if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        ensure_dyn_smem(k, sm);
         k<<<grid, 256, sm, st>>>((float *)dst, (const float *)src, (const float *)Q, rows, D, transpose);
     }
     return cudaGetLastError();

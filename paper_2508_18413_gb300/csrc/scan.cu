@@ -13,9 +13,11 @@
 // iterate poisoned by an overflow would otherwise stop the Newton iteration from progressing.
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace pm {
 
@@ -524,9 +526,212 @@ scan_diag_rows_kernel(int T, int D, int NSUB, const S *__restrict__ a, const S *
     finish_tile(ctl, ntiles);
 }
 
+// ==========================================================================================
+// Diagonal scan, D <= 32, staged through shared memory by bulk copies.  One thread issues
+// cp.async.bulk copies of the tile's a, b and s (one mbarrier; the sub-16-byte tail of a ragged
+// last tile is loaded by plain loads), so every element is read from HBM exactly once.  Rows
+// are then scanned from shared memory as in the register-resident kernel: pass 1 composes the
+// warp aggregates, the block look-back finds the carry, pass 2 recomputes each row's prefix,
+// applies the carry and streams s out.  Tiles of about 8K elements keep two or three CTAs
+// resident per SM, so one CTA's look-back overlaps another's copies.
+// ==========================================================================================
+template <typename R, typename S>
+__global__ void __launch_bounds__(256)
+scan_diag_staged_kernel(int T, int D, int TT, const S *__restrict__ a, const S *__restrict__ b,
+                        R *__restrict__ s, const R *__restrict__ s_reset, unsigned int *flags,
+                        R *__restrict__ gagg, R *__restrict__ gincl, ScanCtl *ctl,
+                        EvalStats *stats, const int *skip, unsigned int spin_limit) {
+    if (skip && *(volatile const int *)skip) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ unsigned int s_tile, s_epoch;
+    __shared__ R wA[8][32], wB[8][32];
+    __shared__ R cin[8][32];
+    __shared__ R tA[32], tB[32], ccar[32];
+    const int P = 32 / D, L = P * D;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned int ntiles = (unsigned int)ceil_div(T, TT);
+    const uint32_t mbar = tc::smem_u32(&s_mbar);
+    if (threadIdx.x == 0) {  // initialised before the CTA barrier inside take_tile: no thread
+        tc::mbar_init(mbar, 1);  // touches the mbarrier before its initialisation is visible
+        tc::fence_barrier_init();
+    }
+    const int tile = (int)take_tile(ctl, &s_tile, &s_epoch);
+    const unsigned int epoch = s_epoch;
+    const long long t0 = (long long)tile * TT;
+    const int TTv = (int)min((long long)TT, (long long)T - t0);
+    const int Ev = TTv * D;
+    const size_t E = (size_t)TT * D;
+    const size_t ab_region = (E * sizeof(S) + 15) & ~(size_t)15;
+    S *sa = reinterpret_cast<S *>(smem_raw);
+    S *sbv = reinterpret_cast<S *>(smem_raw + ab_region);
+    R *ss = reinterpret_cast<R *>(smem_raw + 2 * ab_region);
+    const size_t base = (size_t)t0 * D;
+    const uint32_t ab_bytes = (uint32_t)(((size_t)Ev * sizeof(S)) & ~(size_t)15);
+    const uint32_t s_bytes = (uint32_t)(((size_t)Ev * sizeof(R)) & ~(size_t)15);
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(mbar, 2 * ab_bytes + s_bytes);
+        if (ab_bytes) {
+            tc::bulk_g2s(tc::smem_u32(sa), a + base, ab_bytes, mbar);
+            tc::bulk_g2s(tc::smem_u32(sbv), b + base, ab_bytes, mbar);
+        }
+        if (s_bytes) tc::bulk_g2s(tc::smem_u32(ss), s + base, s_bytes, mbar);
+    }
+    for (int e = (int)(ab_bytes / sizeof(S)) + threadIdx.x; e < Ev; e += 256) {
+        sa[e] = a[base + e];
+        sbv[e] = b[base + e];
+    }
+    for (int e = (int)(s_bytes / sizeof(R)) + threadIdx.x; e < Ev; e += 256) ss[e] = s[base + e];
+    // the copies complete on their own; the bound only guards against a lost completion
+    if (!tc::mbar_wait_drain(mbar, 0, 1u << 24) && threadIdx.x == 0) atomicExch(&ctl->timeout, 1u);
+    __syncthreads();
+
+    const bool lane_on = lane < L;
+    const int d = lane_on ? lane % D : 0;
+    const int tsub = lane_on ? lane / D : 0;
+    const int last_lane = (P - 1) * D + d;
+    const int RW = TT / (8 * P);  // rows per warp
+    const int tw = w * RW * P;    // first local timestep of the warp
+
+    // pass 1: warp aggregates from shared memory
+    R WA = R(1), WB = R(0);
+#pragma unroll 4
+    for (int r = 0; r < RW; r++) {
+        const int tl = tw + r * P + tsub;
+        const bool in = lane_on && tl < TTv;
+        R ra = in ? load_as<S, R>(sa + tl * D + d) : R(1);
+        R rb = in ? load_as<S, R>(sbv + tl * D + d) : R(0);
+        for (int off = D; off < L; off <<= 1) {
+            const R pa = __shfl_up_sync(0xffffffffu, ra, off);
+            const R pb = __shfl_up_sync(0xffffffffu, rb, off);
+            if (lane_on && lane >= off) {
+                rb = ra * pb + rb;
+                ra = ra * pa;
+            }
+        }
+        const R ea = __shfl_sync(0xffffffffu, ra, last_lane);
+        const R eb = __shfl_sync(0xffffffffu, rb, last_lane);
+        WB = ea * WB + eb;
+        WA = ea * WA;
+    }
+    if (lane < D) {
+        wA[w][lane] = WA;
+        wB[w][lane] = WB;
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        const int dd = threadIdx.x;
+        R TA_ = R(1), TB_ = R(0);
+        for (int q = 0; q < 8; q++) {
+            TB_ = wA[q][dd] * TB_ + wB[q][dd];
+            TA_ = wA[q][dd] * TA_;
+        }
+        tA[dd] = TA_;
+        tB[dd] = TB_;
+        if (tile == 0) {
+            gincl[dd] = TB_;
+        } else {
+            gagg[((size_t)tile * 2) * D + dd] = TA_;
+            gagg[((size_t)tile * 2 + 1) * D + dd] = TB_;
+        }
+        ccar[dd] = R(0);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
+    if (tile > 0) {
+        lookback_block<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
+        if (threadIdx.x < D) {
+            gincl[(size_t)tile * D + threadIdx.x] = tA[threadIdx.x] * ccar[threadIdx.x] + tB[threadIdx.x];
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, kFlagIncl));
+    }
+    if (threadIdx.x < D) {
+        const int dd = threadIdx.x;
+        R pa = R(1), pb = R(0);
+        const R c = ccar[dd];
+        for (int q = 0; q < 8; q++) {
+            cin[q][dd] = pa * c + pb;
+            pb = wA[q][dd] * pb + wB[q][dd];
+            pa = wA[q][dd] * pa;
+        }
+    }
+    __syncthreads();
+    // pass 2: rows in order from the carry; s streamed out
+    R delta = lane_on ? cin[w][d] : R(0);
+    R dmax = R(0);
+    unsigned int resets = 0;
+#pragma unroll 4
+    for (int r = 0; r < RW; r++) {
+        const int tl = tw + r * P + tsub;
+        const bool in = lane_on && tl < TTv;
+        R ra = in ? load_as<S, R>(sa + tl * D + d) : R(1);
+        R rb = in ? load_as<S, R>(sbv + tl * D + d) : R(0);
+        for (int off = D; off < L; off <<= 1) {
+            const R pa = __shfl_up_sync(0xffffffffu, ra, off);
+            const R pb = __shfl_up_sync(0xffffffffu, rb, off);
+            if (lane_on && lane >= off) {
+                rb = ra * pb + rb;
+                ra = ra * pa;
+            }
+        }
+        const R dl = ra * delta + rb;
+        if (in) {
+            const int e = tl * D + d;
+            R sn = ss[e] + dl;
+            if (!finite(sn)) {
+                sn = s_reset ? s_reset[d] : R(0);
+                resets++;
+            } else {
+                dmax = max(dmax, fabs(dl));
+            }
+            __stcs(s + base + e, sn);
+        }
+        delta = __shfl_sync(0xffffffffu, dl, last_lane);
+    }
+    if (stats) {
+        double dm = warp_max((double)dmax);
+        unsigned int rsum = warp_sum(resets);
+        if (lane == 0) {
+            if (dm > 0) atomic_max_d(&stats->dmax, dm);
+            if (rsum) atomicAdd(&stats->resets, (unsigned long long)rsum);
+        }
+    }
+    finish_tile(ctl, ntiles);
+}
+
+
+
+// Timesteps per tile of the staged kernel: about 8K elements (4K in FP64), a multiple of the
+// 8 P timesteps of a CTA's rows (P = 32 / D), and small enough to give every SM two tiles.
+static int staged_tile(int T, int D, int elem_bytes) {
+    const int P = 32 / D, unit = 8 * P;
+    const int target = (elem_bytes >= 8 ? 4096 : 8192) / D;
+    int tt = std::max(unit, target / unit * unit);
+    const int spread = ceil_div(ceil_div(T, 2 * 152), unit) * unit;
+    return std::max(unit, std::min(tt, spread));
+}
+
+static size_t staged_smem(int TT, int D, int rbytes, int sbytes) {
+    const size_t E = (size_t)TT * D;
+    return 2 * ((E * sbytes + 15) & ~(size_t)15) + E * rbytes;
+}
+
+// The register-resident kernel is the default (measured faster on GB300 at 2^20..2^28
+// elements); PMCMC_SCAN_KERNEL=staged selects the bulk-copy staged kernel (measurements).
+static bool staged_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("PMCMC_SCAN_KERNEL");
+        v = (e && strcmp(e, "staged") == 0) ? 1 : 0;
+    }
+    return v == 1;
+}
 
 int diag_scan_tile(int T, int D, int elem_bytes) {
-    if (D <= 32) return diag_scan_tile_rows(T, D);
+    if (D <= 32) return std::min(diag_scan_tile_rows(T, D), staged_tile(T, D, elem_bytes));
     // enough tiles to fill the GPU twice over, at most ~4096 elements (FP32) per tile
     const int max_elems = elem_bytes >= 8 ? 2048 : 4096;
     int tt_max = std::max(8, (max_elems / std::max(D, 1)) / 8 * 8);
@@ -549,10 +754,8 @@ static cudaError_t run_scan_diag(int T, int D, int TT, const void *a, const void
     const int ntiles = ceil_div(T, TT);
     size_t sm = diag_smem(TT, D, sizeof(R));
     auto k = scan_diag_kernel<R, S>;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = ensure_dyn_smem(k, sm);
+    if (e != cudaSuccess) return e;
     k<<<ntiles, kScanThreads, sm, st>>>(T, D, TT, (const S *)a, (const S *)b, (R *)s,
                                         (const R *)s_reset, w.flags, (R *)w.agg, (R *)w.incl,
                                         w.ctl, stats, skip, spin);
@@ -631,10 +834,35 @@ int diag_scan_tile_rows(int T, int D) {
     return 8 * rows * nsub * (32 / D);
 }
 
+template <typename R, typename S>
+static cudaError_t run_scan_staged(int T, int D, const void *a, const void *b, void *s,
+                                   const void *s_reset, const ScanWork &w, EvalStats *stats,
+                                   const int *skip, unsigned int spin, cudaStream_t st) {
+    const int TT = staged_tile(T, D, sizeof(R));
+    const int ntiles = ceil_div(T, TT);
+    if (ntiles > w.max_tiles) return cudaErrorInvalidValue;
+    const size_t sm = staged_smem(TT, D, sizeof(R), sizeof(S));
+    auto k = scan_diag_staged_kernel<R, S>;
+    cudaError_t e = ensure_dyn_smem(k, sm);
+    if (e != cudaSuccess) return e;
+    prefer_shared(k);
+    k<<<ntiles, 256, sm, st>>>(T, D, TT, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset,
+                               w.flags, (R *)w.agg, (R *)w.incl, w.ctl, stats, skip, spin);
+    return cudaGetLastError();
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, const void *a,
                              const void *b, void *s, const void *s_reset, const ScanWork &w,
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st) {
+    if (D <= 32 && staged_enabled() && aligned16(a) && aligned16(b) && aligned16(s)) {
+        if (f64) return run_scan_staged<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+        if (storage == 1)
+            return run_scan_staged<float, __nv_bfloat16>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+        return run_scan_staged<float, float>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+    }
     if (D <= 32) {
         if (f64) return run_scan_rows<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
         if (storage == 1)

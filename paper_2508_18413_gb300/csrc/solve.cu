@@ -163,6 +163,7 @@ void pmcmc_options_default(pmcmc_options *o) {
     o->seed = 0;
     o->chain_id = 0;
     o->spin_limit = 0;
+    o->engine = 0;
 }
 
 pmcmc_status pmcmc_create(pmcmc_ctx **out, int device) {
@@ -377,12 +378,21 @@ void fill_eval_args(EvalArgs &A, const pmcmc_target *tg, const pmcmc_options *o,
     A.y = tg->y;
     A.seed = o->seed;
     A.chain = o->chain_id;
+    A.engine = o->engine;
+}
+
+// Whether the evaluate pass of this problem runs on the tensor-core kernel.
+static bool uses_tc(const pmcmc_target *tg, const pmcmc_options *o, int T) {
+    EvalArgs A;
+    fill_eval_args(A, tg, o, T);
+    return logreg_tc_supported(A);
 }
 
 // Workspace plan for one solve.
 struct Plan {
     size_t o_a = 0, o_b = 0, o_xi = 0, o_u = 0, o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0;
-    size_t o_flags = 0, o_agg = 0, o_incl = 0, o_tmp = 0;
+    size_t o_flags = 0, o_agg = 0, o_incl = 0, o_tmp = 0, o_img = 0;
+    bool tc = false;
     int tiles = 0, tile_t = 0;
     size_t bytes = 0;
 };
@@ -406,6 +416,8 @@ static Plan make_plan(const pmcmc_target *tg, const pmcmc_options *o, int T, boo
         const int DP = logreg_padded_dim(D);
         const int Npad = ceil_div(tg->N, 64) * 64;
         p.o_xp = cv.take((size_t)rb * Npad * DP);
+        p.tc = uses_tc(tg, o, T);
+        if (p.tc) p.o_img = cv.take(logreg_tc_image_bytes(tg->N));
         if (dense) {
             p.o_w = cv.take((size_t)rb * T * tg->N);
             p.o_ru = cv.take((size_t)rb * T * D);
@@ -601,6 +613,10 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
                                                                      D, Npad, DP, rb);
         PM_CUDA(c, cudaGetLastError());
         prof_count(c);
+        if (p.tc) {
+            PM_CUDA(c, launch_logreg_tc_pack(tg->X, tg->y, tg->N, D, base + p.o_img, st));
+            prof_count(c);
+        }
     }
     // initial guess: s^(0) = s_init, or s0 broadcast (Appendix B)
     if (s_init) {
@@ -641,17 +657,20 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     A.iter = &c->ctl->iter;
     const int max_iters = o->max_iters > 0 ? o->max_iters : T;
     const unsigned int spin = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
+    if (p.tc) A.tc_img = base + p.o_img;
+    A.timeout = &c->ctl->scan.timeout;
+    A.spin_limit = spin;
     const double atol = o->atol;
 
     CtlBlock *h = c->host_ctl;
     if (!c->prof_on && !c->no_graph) {
         char kb[768];
         snprintf(kb, sizeof(kb),
-                 "%llu|%d|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%d|%.17g|%d|%d|%.17g|%.17g|%d|%u|%llu|%u|"
+                 "%llu|%d|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%d|%.17g|%d|%d|%.17g|%.17g|%d|%u|%llu|%u|%d|"
                  "%p|%p|%p|%p|%p|%p|%p|%p|%p",
                  c->ws_generation, T, D, tg->N, (int)tg->kind, (int)o->sampler, o->leapfrog_L,
                  (int)o->jac, o->step, tg->prior_scale, (int)o->precision, o->damping, o->clip,
-                 o->gate_grad, o->atol, o->rtol, max_iters, spin, o->seed, o->chain_id, s0, s_out,
+                 o->gate_grad, o->atol, o->rtol, max_iters, spin, o->seed, o->chain_id, o->engine, s0, s_out,
                  xi, (const void *)u, tg->mean, tg->prec, tg->X, tg->y, (void *)base);
         pmcmc_status gs = build_loop_graph(c, kb, tg, o, A, p, w, s_out, s0, max_iters, spin);
         if (gs == PMCMC_OK) {
@@ -670,7 +689,7 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
                 unsigned int zero = 0;
                 cudaMemcpy(&c->ctl->scan.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice);
                 status = PMCMC_ETIMEOUT;
-                fail(c, status, "a look-back wait in the scan ran out");
+                fail(c, status, "a bounded wait (scan look-back or evaluate pipeline) ran out");
             }
             if (res) {
                 res->iters = h->iter;
@@ -744,7 +763,7 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         unsigned int zero = 0;
         cudaMemcpy(&c->ctl->scan.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice);
         status = PMCMC_ETIMEOUT;
-        fail(c, status, "a look-back wait in the scan ran out");
+        fail(c, status, "a bounded wait (scan look-back or evaluate pipeline) ran out");
     }
     if (res) {
         res->iters = it;
@@ -781,11 +800,13 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
     const bool f64 = o->precision == PMCMC_F64;
     const int rb = f64 ? 8 : 4;
     Carve cv;
-    size_t o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0, o_j = 0;
+    size_t o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0, o_j = 0, o_img = 0;
     const bool dense = o->jac == PMCMC_JAC_DENSE;
+    const bool tc = uses_tc(tg, o, T);
     if (tg->kind == PMCMC_LOGREG) {
         const int DP = logreg_padded_dim(D);
         o_xp = cv.take((size_t)rb * ceil_div(tg->N, 64) * 64 * DP);
+        if (tc) o_img = cv.take(logreg_tc_image_bytes(tg->N));
         if (dense) {
             o_w = cv.take((size_t)rb * T * tg->N);
             o_ru = cv.take((size_t)rb * T * D);
@@ -814,6 +835,12 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
         A.Xp = base + o_xp;
         pad_rows_kernel<<<grid_for((size_t)Npad * DP), 256, 0, st>>>(base + o_xp, tg->X, tg->N, D,
                                                                      Npad, DP, rb);
+        if (tc) {
+            PM_CUDA(c, launch_logreg_tc_pack(tg->X, tg->y, tg->N, D, base + o_img, st));
+            A.tc_img = base + o_img;
+            A.timeout = &c->ctl->scan.timeout;
+            A.spin_limit = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
+        }
         if (dense) {
             A.w_out = base + o_w;
             A.rank1_u = base + o_ru;
@@ -826,6 +853,15 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
         PM_CUDA(c, launch_eval_small(A, st));
     }
     PM_CUDA(c, cudaStreamSynchronize(st));
+    if (tc) {
+        unsigned int to = 0;
+        PM_CUDA(c, cudaMemcpy(&to, &c->ctl->scan.timeout, sizeof(to), cudaMemcpyDeviceToHost));
+        if (to) {
+            const unsigned int zero = 0;
+            cudaMemcpy(&c->ctl->scan.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+            return fail(c, PMCMC_ETIMEOUT, "a bounded wait of the evaluate pipeline ran out");
+        }
+    }
     return PMCMC_OK;
 }
 

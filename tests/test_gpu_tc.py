@@ -1,0 +1,163 @@
+"""Tensor-core evaluate-and-linearise of MALA on logistic regression (tcgen05, kind::tf32 split
+into three products) against the FP64 oracle, and against the CUDA-core kernel.
+
+Bars: FP32 states within 1e-5 (1 + |s|) of the oracle with identical accept decisions away
+from near-ties (oracle margin |min(0, ell) - log u| < 1e-4 may flip under FP32 rounding);
+the diagonal Jacobian within 2e-3 (it only shapes the Newton step; its Hessian term is one tf32
+product)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2508_18413_gb300 as P
+
+DEV = "cuda:0"
+
+
+def cu(x, dtype=torch.float32):
+    return torch.tensor(np.asarray(x), dtype=dtype, device=DEV)
+
+
+def npy(t):
+    return t.detach().cpu().double().numpy()
+
+
+def pair(N, D, seed):
+    X, y, _ = W.blr_data(N, D, seed=seed)
+    X = X.astype(np.float32).astype(np.float64)
+    return (O.Target("logreg", D, X=X, y=y, sigma_p=1.0),
+            P.Target("logreg", D, X=cu(X), y=cu(y), prior_scale=1.0))
+
+
+def fnoise(T, D, seed):
+    xi, u = W.noise(T, D, seed=seed)
+    return xi.astype(np.float32).astype(np.float64), u
+
+
+def _lin(gt, opt, T, s0, s, xi, u):
+    f, J, acc, ell = P.pmcmc_linearize(gt, opt, T, cu(s0), cu(s), cu(xi), cu(u, torch.float64))
+    return npy(f), npy(J), npy(acc).astype(bool), npy(ell)
+
+
+# steps chosen so that both branches of the accept test occur at these states
+@pytest.mark.parametrize("N,D,T,eps", [(1000, 25, 300, 0.01), (70, 4, 97, 0.1),
+                                       (130, 32, 129, 0.05), (33, 1, 64, 0.3),
+                                       (257, 17, 1, 0.01)])
+@pytest.mark.parametrize("jac", ["diag", "zero"])
+def test_tc_linearize_matches_oracle(N, D, T, eps, jac):
+    ot, gt = pair(N, D, seed=N + D)
+    rng = np.random.default_rng(D)
+    s = (rng.standard_normal((T, D)) * 0.15).astype(np.float32).astype(np.float64)
+    s0 = (rng.standard_normal(D) * 0.15).astype(np.float32).astype(np.float64)
+    xi, u = fnoise(T, D, seed=D + 1)
+    opt = P.Options(sampler="mala", step=eps, jac=jac, precision="f32", gate_grad=0)
+    f, J, acc, ell = _lin(gt, opt, T, s0, s, xi, u)
+    p = O.Problem(ot, "mala", eps, xi=xi, u=u, gate_grad=0)
+    logu = np.log(u)
+    checked = 0
+    for t in range(T):
+        prev = s0 if t == 0 else s[t - 1]
+        fo, ello, acco = O.f(p, t + 1, prev)
+        if abs(min(0.0, ello) - logu[t]) < 1e-4:
+            continue
+        checked += 1
+        assert acc[t] == acco, (t, ello, logu[t], ell[t])
+        np.testing.assert_allclose(f[t], fo, rtol=1e-5, atol=1e-5)
+        assert ell[t] == pytest.approx(ello, rel=1e-4, abs=2e-4)
+        if jac == "diag":
+            np.testing.assert_allclose(J[t], np.diag(O.jacobian(p, t + 1, prev, "diag")),
+                                       rtol=2e-3, atol=2e-3)
+        else:
+            assert np.all(J[t] == 0)
+    assert checked >= max(1, T // 2)
+    assert 0 < acc.sum() < T or T < 4   # both branches exercised on the larger cases
+
+
+def test_tc_and_cuda_core_kernels_agree():
+    N, D, T = 1000, 25, 1000
+    ot, gt = pair(N, D, seed=3)
+    rng = np.random.default_rng(7)
+    s = (rng.standard_normal((T, D)) * 0.1).astype(np.float32).astype(np.float64)
+    s0 = np.zeros(D)
+    xi, u = fnoise(T, D, seed=9)
+    res = []
+    for engine in ("auto", "simt"):
+        opt = P.Options(sampler="mala", step=0.01, jac="diag", precision="f32", gate_grad=0,
+                        engine=engine)
+        res.append(_lin(gt, opt, T, s0, s, xi, u))
+    (f1, J1, a1, e1), (f2, J2, a2, e2) = res
+    close = np.abs(np.minimum(e2, 0) - np.log(u)) < 1e-4
+    assert np.all(a1[~close] == a2[~close])
+    np.testing.assert_allclose(f1[~close], f2[~close], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(J1[~close], J2[~close], rtol=2e-3, atol=2e-3)
+
+
+@pytest.mark.parametrize("N,D,T,seed", [(150, 6, 600, 5), (1000, 25, 1000, 1)])
+def test_tc_solve_matches_oracle_chain(N, D, T, seed):
+    ot, gt = pair(N, D, seed=2)
+    xi, u = fnoise(T, D, seed=seed)
+    eps = 0.01
+    ref, ell, acc = O.chain(O.Problem(ot, "mala", eps, xi=xi, u=u), T, np.zeros(D))
+    opt = P.Options(sampler="mala", step=eps, jac="diag", precision="f32", atol=1e-6, clip=1,
+                    gate_grad=0)
+    s, res = P.pmcmc_solve(gt, opt, T, cu(np.zeros(D)), xi=cu(xi), u=cu(u, torch.float64))
+    assert res["status"] == "OK" and res["iters"] <= T
+    s = npy(s)
+    margin = np.abs(np.minimum(ell, 0.0) - np.log(u))
+    ties = np.nonzero(margin < 1e-4)[0]
+    upto = ties[0] if len(ties) else T
+    assert upto >= min(T, 300)
+    err = np.abs(s[:upto] - ref[:upto])
+    assert np.all(err <= 1e-5 * (1 + np.abs(ref[:upto]))), np.max(err)
+
+
+def test_tc_bf16_scan_pairs_solve():
+    N, D, T = 200, 8, 500
+    ot, gt = pair(N, D, seed=4)
+    xi, u = fnoise(T, D, seed=2)
+    ref, ell, _ = O.chain(O.Problem(ot, "mala", 0.01, xi=xi, u=u), T, np.zeros(D))
+    opt = P.Options(sampler="mala", step=0.01, jac="diag", precision="f32_scan_bf16", atol=1e-6,
+                    clip=1, gate_grad=0)
+    s, res = P.pmcmc_solve(gt, opt, T, cu(np.zeros(D)), xi=cu(xi), u=cu(u, torch.float64))
+    assert res["status"] == "OK"
+    s = npy(s)
+    margin = np.abs(np.minimum(ell, 0.0) - np.log(u))
+    ties = np.nonzero(margin < 1e-4)[0]
+    upto = ties[0] if len(ties) else T
+    assert np.all(np.abs(s[:upto] - ref[:upto]) <= 1e-5 * (1 + np.abs(ref[:upto])))
+
+
+def test_tc_wait_bound_returns_timeout_and_context_recovers():
+    """Every wait of the tensor-core pipeline is bounded: with a one-poll bound the waits run
+    out, the launch drains its copies and MMAs, frees its tensor memory and reports ETIMEOUT;
+    the same context then solves correctly."""
+    N, D, T = 1000, 25, 2048
+    ot, gt = pair(N, D, seed=6)
+    xi, u = fnoise(T, D, seed=3)
+    seen = False
+    for _ in range(3):
+        opt = P.Options(sampler="mala", step=0.01, jac="diag", precision="f32", atol=1e-6,
+                        clip=1, gate_grad=0, spin_limit=1, max_iters=2)
+        try:
+            P.pmcmc_solve(gt, opt, T, cu(np.zeros(D)), xi=cu(xi), u=cu(u, torch.float64))
+        except P.PmcmcError as e:
+            assert e.status == -4
+            seen = True
+    assert seen
+    T2 = 400
+    ref, ell, _ = O.chain(O.Problem(ot, "mala", 0.01, xi=xi[:T2], u=u[:T2]), T2, np.zeros(D))
+    opt = P.Options(sampler="mala", step=0.01, jac="diag", precision="f32", atol=1e-6, clip=1,
+                    gate_grad=0)
+    s, res = P.pmcmc_solve(gt, opt, T2, cu(np.zeros(D)), xi=cu(xi[:T2]), u=cu(u[:T2], torch.float64))
+    assert res["status"] == "OK"
+    margin = np.abs(np.minimum(ell, 0.0) - np.log(u[:T2]))
+    ties = np.nonzero(margin < 1e-4)[0]
+    upto = ties[0] if len(ties) else T2
+    s = npy(s)
+    assert np.all(np.abs(s[:upto] - ref[:upto]) <= 1e-5 * (1 + np.abs(ref[:upto])))
