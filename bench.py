@@ -44,9 +44,23 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # the stop-gradient gate term add two Hessian-vector products (2 N D MACs each): 18 N D flops.
 def alg_flops_per_t(gate_grad: int) -> int:
     return (18 if gate_grad else 10) * WL.N * WL.D
-# DRAM traffic of one evaluate-and-linearise launch from the committed ncu capture
-# (profiles/eval_logreg_c2.md); None until that capture exists for the current kernel.
-EVAL_TRAFFIC_BYTES = None
+
+
+def tensor_peak_fp32_equiv():
+    """The tensor-core kernel computes its FP32 contractions as three tf32 products; its peak in
+    FP32-equivalent flops is the tf32 dense rate / 3, the tf32 rate being the measured bf16 rate
+    x the nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+        src = "measured bf16 (MEASURED_PEAKS.json)"
+    except Exception:
+        bf16, src = 1900.0, "fallback bf16 1.9 PFLOP/s"
+    return bf16 * (1.1 / 2.25) / 3.0, src
+
+
+# DRAM traffic of one launch of the dominant kernel (eval_logreg_tc_kernel) from the committed
+# ncu capture (profiles/eval_logreg_tc_c2.md): 4.16 MB read, 0 written (the outputs stay in L2).
+EVAL_TRAFFIC_BYTES = 4159744
 
 
 def parse():
@@ -349,6 +363,11 @@ def run_ours(args):
 
     avg_eval_ms = prof["eval_ms"] / max(1, prof["eval_launches"])
     achieved = alg_flops_per_t(args.gate_grad) * WL.T / (avg_eval_ms / 1000.0) / 1e12
+    tc = args.gate_grad == 0 and WL.D <= 32     # the tensor-core kernel runs this workload
+    if tc:
+        peak, peak_src = tensor_peak_fp32_equiv()
+    else:
+        peak, peak_src = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
     last = results[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -365,10 +384,13 @@ def run_ours(args):
         "e2e": {"value": job_value(world, WL.T, e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "eval_logreg_kernel (evaluate and linearise)",
-                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": EVAL_TRAFFIC_BYTES,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+        "roofline": {"bound": "tensor" if tc else "alu",
+                     "kernel": ("eval_logreg_tc_kernel (evaluate and linearise, tcgen05 3xTF32)"
+                                if tc else "eval_logreg_kernel (evaluate and linearise)"),
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": EVAL_TRAFFIC_BYTES if tc else None,
+                     "peak_source": peak_src + (" x 1.1/2.25 (tf32) / 3 (three products)" if tc else ""),
+                     "achieved_is": "algorithmic FP32 flops (10 N D per timestep) / launch time",
                      "avg_launch_ms": avg_eval_ms, "launches": prof["eval_launches"],
                      "timing": "CUDA events around each launch, stream of the launch, "
                                f"{args.steps} profiled solves after the timed region",
