@@ -22,15 +22,17 @@
 //              the A operand of G and H.  Each warpgroup forms its dimensions of the proposal,
 //              of the residual and of J; the MH log-ratio (FP64) is summed over the four
 //              warpgroups through shared memory.
-//   warp 16    allocates TMEM and issues every MMA from one thread.
-//   warp 17    one thread streams pre-swizzled design chunks with bulk copies (3 stages).
-// TMEM: Z double buffered (columns 0-31, 32-63); G per chunk, double buffered (64-95, 96-127);
-// H accumulated over the chunks (128-159).  The tensor core's FP32 accumulation truncates, so
+//   warps 16-17 issue the MMAs, one thread each: the Z products, and the G and H products;
+//              warp 16 allocates and frees TMEM, and its lane 1 streams pre-swizzled design
+//              chunks with bulk copies (4 stages).
+// TMEM: Z in three buffers, G per chunk in two buffers, H accumulated over the chunks.  The tensor core's FP32 accumulation truncates, so
 // a sum over all N rows in one accumulator would drift by up to an ulp of |G| per MMA; each
 // chunk's G product therefore starts a fresh accumulator and the epilogue adds the 32-row
 // partials in registers with round-to-nearest.  Every wait is bounded: a wait that runs out
 // raises the CTA's abort flag, the roles finish without further work, in-flight copies and
 // MMAs are drained, TMEM is freed and the launch's timeout word is set.
+#include <type_traits>
+
 #include "common.cuh"
 #include "eval.h"
 #include "internal.h"
@@ -45,20 +47,23 @@ using namespace tc;
 constexpr int kM = 128;                        // timesteps per CTA (MMA M; one TMEM lane each)
 constexpr int kNB = 32;                        // design rows per chunk
 constexpr int kDP = 32;                        // padded feature dimension
-constexpr int kStages = 3;                     // chunk images in flight
+constexpr int kStages = 4;                     // chunk images in flight
 constexpr int kGroups = 4;                     // epilogue warpgroups
 constexpr int kCols = kDP / kGroups;           // columns / dimensions per warpgroup: 8
 constexpr int kEpiWarps = 4 * kGroups;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = kEpiThreads + 64;     // + MMA warp + copy warp
-constexpr int kMmaWarp = kEpiWarps, kCopyWarp = kEpiWarps + 1;
+constexpr int kThreads = kEpiThreads + 64;     // + two MMA-issue warps (one lane copies)
+// MMA issuers (lane 0 of each): the Z products, and the G and H products
+constexpr int kIssZ = kEpiWarps, kIssG = kEpiWarps + 1;
+constexpr int kMmaWarp = kIssZ;                // allocates / frees TMEM
+constexpr int kCopyWarp = kIssZ, kCopyLane = 1;  // the bulk-copy producer: lane 1 of warp 16
 constexpr int kOp = kNB * kDP * 4;             // one 32 x 32 operand block: 4096 bytes
 constexpr int kImg = 5 * kOp + kNB * 4;        // chunk image: X hi, X lo, X^T hi, X^T lo, (X.X)^T hi, y
 constexpr int kStageStride = 21504;            // 1024-aligned stage slot
 constexpr int kRowOp = kM * kDP * 4;           // a 128 x 32 A operand: 16384 bytes
 constexpr uint32_t kIdesc = idesc_tf32(kM, 32);
 constexpr uint32_t kTmemCols = 256;
-constexpr unsigned int kDrainLimit = 1u << 22;
+constexpr unsigned int kDrainLimit = 1u << 20;  // polls of up to ~2 us each
 
 // shared-memory map, offsets from a 1024-aligned base
 constexpr int oVhi = 0, oVlo = kRowOp;         // A operand of Z: the states (x, then x~)
@@ -66,7 +71,11 @@ constexpr int oCW = 2 * kRowOp;                // 2 buffers of (C hi, C lo, W hi
 constexpr int kCWStride = 3 * kRowOp;
 constexpr int oStage = oCW + 2 * kCWStride;
 constexpr int oBar = oStage + kStages * kStageStride;
-constexpr int bFull = 0, bEmpty = kStages, bZfull = 2 * kStages, bCfull = bZfull + 2,
+constexpr int kZbuf = 3;                       // Z buffers in TMEM (GEMM1 runs 3 chunks ahead)
+constexpr uint32_t kColZ = 0;                  // Z: 3 buffers of 32 columns
+constexpr uint32_t kColG = 32 * kZbuf;         // G: 2 buffers of 32 columns (fresh per chunk)
+constexpr uint32_t kColH = kColG + 64;         // H: 32 columns
+constexpr int bFull = 0, bEmpty = kStages, bZfull = 2 * kStages, bCfull = bZfull + kZbuf,
               bCempty = bCfull + 2, bGdone = bCempty + 2, bVready = bGdone + 1, bFin = bVready + 1,
               kNumBars = bFin + 1;
 constexpr int oMisc = oBar + 8 * kNumBars;     // tmem address, abort flag
@@ -101,12 +110,24 @@ __device__ __forceinline__ void put_row_pair(unsigned char *hi, unsigned char *l
     }
 }
 
-// warp-uniform bounded wait (every lane takes the same branch afterwards)
+// Warp-uniform bounded wait (every lane polls; every lane takes the same branch afterwards).
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort,
                                           unsigned int limit) {
     const bool ok = mbar_wait(bar, parity, abort, limit);
     return __all_sync(0xffffffffu, ok);
 }
+
+// Arrive once per warp after every lane's shared-memory writes (made visible to the tensor
+// core) and TMEM reads are ordered before the warp barrier.
+__device__ __forceinline__ void warp_arrive(uint32_t bar) {
+    fence_async_smem();
+    tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
+template <int P>
+using PassC = std::integral_constant<int, P>;
 
 template <typename S_>
 __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A) {
@@ -128,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
     if (tid == 0) {
         for (int i = 0; i < kNumBars; i++) {
             uint32_t cnt = 1;
-            if (i == bCfull || i == bCfull + 1 || i == bVready) cnt = kEpiThreads;
+            if (i == bCfull || i == bCfull + 1 || i == bVready) cnt = kEpiWarps;  // one per warp
+            if ((i >= bEmpty && i < bEmpty + kStages) || i == bFin) cnt = 2;      // both issuers
             mbar_init(bar(i), cnt);
         }
         *abort_f = 0;
@@ -143,9 +165,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
     tc_fence_after();
     const uint32_t tm = *tmem_slot;
 
-    if (warp == kCopyWarp) {
+    if (warp == kCopyWarp && lane == kCopyLane) {
         // ---------------- producer: chunk images, both passes ----------------
-        if (lane == 0) {
+        {
             const unsigned char *img = static_cast<const unsigned char *>(A.tc_img);
             int k = 0;
             for (; k < 2 * nch; k++) {
@@ -158,16 +180,18 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             for (int q = k > kStages ? k - kStages : 0; q < k; q++)
                 mbar_wait_drain(bar(bFull + q % kStages), (uint32_t)(q / kStages) & 1u, kDrainLimit);
         }
-        __syncwarp();
-    } else if (warp == kMmaWarp) {
-        // ---------------- MMA issue (one thread) ----------------
+    } else if (warp == kIssZ) {
+        // ---------------- Z = V X^T issue (one thread per product stream) ----------------
+        // Issuing from two threads lets the Z and the G products of different chunks overlap.
+        // GEMM1 runs kZbuf chunks ahead: Z(k + 3) reuses the buffer of Z(k), which the epilogue
+        // has loaded (prefetch) before it signals C(k) ready.
         if (lane == 0) {
             auto issue_z = [&](int k) -> bool {
                 const int s = k % kStages;
                 if (!mbar_wait(bar(bFull + s), (uint32_t)(k / kStages) & 1u, abort_f, limit)) return false;
                 tc_fence_after();
                 const uint32_t st = sb + oStage + s * kStageStride;
-                const uint32_t zt = tm + (uint32_t)(k & 1) * 32u;
+                const uint32_t zt = tm + kColZ + (uint32_t)(k % kZbuf) * 32u;
 #pragma unroll
                 for (int kk = 0; kk < 4; kk++) {
                     const uint64_t ah = sdesc(sb + oVhi + 32 * kk), al = sdesc(sb + oVlo + 32 * kk);
@@ -176,7 +200,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     mma_tf32(zt, ah, bl, kIdesc, 1);
                     mma_tf32(zt, ah, bh, kIdesc, 1);
                 }
-                mma_commit(bar(bZfull + (k & 1)));
+                mma_commit(bar(bZfull + k % kZbuf));
+                mma_commit(bar(bEmpty + s));  // this issuer is done with the stage
                 return true;
             };
             bool ok = true;
@@ -185,15 +210,30 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 if (!ok) break;
                 tc_fence_after();
                 const int kb = pass * nch;
-                ok = issue_z(kb);
+                for (int j = 0; j < kZbuf && j < nch && ok; j++) ok = issue_z(kb + j);
+                for (int j = 0; j + kZbuf < nch && ok; j++) {
+                    const int k = kb + j;
+                    if (!(ok = mbar_wait(bar(bCfull + (k & 1)), (uint32_t)(k >> 1) & 1u, abort_f, limit))) break;
+                    tc_fence_after();
+                    ok = issue_z(k + kZbuf);
+                }
+            }
+            mma_commit(bar(bFin));
+            mbar_wait_drain(bar(bFin), 0, kDrainLimit);
+        }
+    } else if (warp == kIssG) {
+        // ---------------- G = C X and H = W (X.X) issue ----------------
+        if (lane == 0) {
+            bool ok = true;
+            for (int pass = 0; pass < 2 && ok; pass++) {
+                const int kb = pass * nch;
                 for (int j = 0; j < nch && ok; j++) {
                     const int k = kb + j;
-                    if (j + 1 < nch && !(ok = issue_z(k + 1))) break;
                     if (!(ok = mbar_wait(bar(bCfull + (k & 1)), (uint32_t)(k >> 1) & 1u, abort_f, limit))) break;
                     tc_fence_after();
                     const uint32_t st = sb + oStage + (k % kStages) * kStageStride;
                     const uint32_t cw = sb + oCW + (k & 1) * kCWStride;
-                    const uint32_t gt = tm + 64 + (uint32_t)(k & 1) * 32u;  // fresh per chunk
+                    const uint32_t gt = tm + kColG + (uint32_t)(k & 1) * 32u;  // fresh per chunk
 #pragma unroll
                     for (int kk = 0; kk < 4; kk++) {
                         const uint64_t ch = sdesc(cw + 32 * kk), cl = sdesc(cw + kRowOp + 32 * kk);
@@ -205,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     if (pass == 0 && want_dh) {
 #pragma unroll
                         for (int kk = 0; kk < 4; kk++)
-                            mma_tf32(tm + 128, sdesc(cw + 2 * kRowOp + 32 * kk), sdesc(st + 4 * kOp + 32 * kk),
+                            mma_tf32(tm + kColH, sdesc(cw + 2 * kRowOp + 32 * kk), sdesc(st + 4 * kOp + 32 * kk),
                                      kIdesc, (j > 0 || kk > 0) ? 1u : 0u);
                     }
                     mma_commit(bar(bCempty + (k & 1)));
@@ -216,7 +256,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             mma_commit(bar(bFin));
             mbar_wait_drain(bar(bFin), 0, kDrainLimit);
         }
-        __syncwarp();
     } else {
         // ---------------- epilogue warpgroups ----------------
         const int q = warp & 3, h = warp >> 2;
@@ -255,35 +294,56 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             float x[kCols];
             load_x(x);
             put_row_pair(sm + oVhi, sm + oVlo, r, h, x);
-            fence_async_smem();
-            mbar_arrive(bar(bVready));
+            warp_arrive(bar(bVready));
         }
         auto add_partial = [&](int kc) {  // G of chunk kc, own dimensions
             float gp[kCols];
-            tmem_ld8(lrow + 64 + 32u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
+            tmem_ld8(lrow + kColG + 32u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < kCols; i++) gs[i] += gp[i];
         };
-        for (int pass = 0; pass < 2; pass++) {
+        // one pass over the design: chunk loop, then the pass end
+        auto run_pass = [&](auto pc) {
+            constexpr int pass = decltype(pc)::value;
+            constexpr bool kW = pass == 0;  // Hessian weights are needed in pass 1 only
+            // software pipeline: Z(k + 1) and the G partial of chunk k - 2 are loaded from TMEM
+            // while chunk k is computed from registers
+            float zcur[kCols];
+            {
+                const int k = pass * nch;
+                if (ok && (ok = warp_wait(bar(bZfull + k % kZbuf), (uint32_t)(k / kZbuf) & 1u, abort_f, limit))) {
+                    tc_fence_after();
+                    tmem_ld8(lrow + kColZ + (uint32_t)(k % kZbuf) * 32u + (uint32_t)d0, zcur);
+                    tmem_wait_ld();
+                }
+            }
             for (int j = 0; j < nch && ok; j++) {
                 const int k = pass * nch + j, b = k & 1, si = k % kStages;
-                if (!(ok = warp_wait(bar(bZfull + b), (uint32_t)(k >> 1) & 1u, abort_f, limit))) break;
+                float znext[kCols], gp[kCols];
+                const bool more = j + 1 < nch;
+                if (more) {
+                    if (!(ok = warp_wait(bar(bZfull + (k + 1) % kZbuf), (uint32_t)((k + 1) / kZbuf) & 1u, abort_f, limit)))
+                        break;
+                }
+                // G of chunk k - 2 is complete: its C buffer is free and its partial readable
+                if (k >= 2 && !(ok = warp_wait(bar(bCempty + b), (uint32_t)((k - 2) >> 1) & 1u, abort_f, limit)))
+                    break;
                 if (!(ok = warp_wait(bar(bFull + si), (uint32_t)(k / kStages) & 1u, abort_f, limit))) break;
                 tc_fence_after();
-                float z[kCols];
-                tmem_ld8(lrow + (uint32_t)b * 32u + (uint32_t)d0, z);
+                if (more) tmem_ld8(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 32u + (uint32_t)d0, znext);
+                const bool part2 = j >= 2;
+                if (part2) tmem_ld8(lrow + kColG + 32u * (uint32_t)(k & 1) + (uint32_t)d0, gp);
                 const float4 *ys4 = reinterpret_cast<const float4 *>(sm + oStage + si * kStageStride + 5 * kOp) + 2 * h;
                 const float4 ya = ys4[0], yb = ys4[1];
                 const float yv8[kCols] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
-                tmem_wait_ld();
                 float chi[kCols], clo[kCols], whi[kCols];
                 float llc = 0.0f;
                 const int nbase = j * kNB + d0;
                 const bool full = nbase + kCols <= N;
 #pragma unroll
                 for (int i = 0; i < kCols; i++) {
-                    const float zz = z[i];
+                    const float zz = zcur[i];
                     const float yv = yv8[i];
                     const float m = __expf(-fabsf(zz));
                     const float qv = __fdividef(1.0f, 1.0f + m);
@@ -291,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     const float p = zz >= 0.0f ? qv : mq;   // sigmoid(z)
                     const float pc = zz >= 0.0f ? mq : qv;  // 1 - sigmoid(z)
                     float c = yv - p;
-                    float w = p * pc;
+                    float w = kW ? p * pc : 0.0f;
                     float ln = yv * zz - (fmaxf(zz, 0.0f) + __logf(1.0f + m));  // y z - softplus(z)
                     if (!full && nbase + i >= N) {
                         c = 0.0f;
@@ -301,16 +361,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     llc += ln;
                     chi[i] = to_tf32(c);
                     clo[i] = to_tf32(c - chi[i]);
-                    whi[i] = to_tf32(w);
+                    if (kW) whi[i] = to_tf32(w);
                 }
                 if (pass) ll1 += (double)llc;
                 else ll0 += (double)llc;
-                if (k >= 2) {
-                    // G of chunk k - 2 is complete: its C buffer is free and its partial readable
-                    if (!(ok = warp_wait(bar(bCempty + b), (uint32_t)((k - 2) >> 1) & 1u, abort_f, limit))) break;
-                    tc_fence_after();
-                    if (j >= 2) add_partial(k - 2);
-                }
                 unsigned char *cw = sm + oCW + b * kCWStride;
 #pragma unroll
                 for (int c4 = 0; c4 < 2; c4++) {
@@ -319,13 +373,20 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                         make_float4(chi[4 * c4], chi[4 * c4 + 1], chi[4 * c4 + 2], chi[4 * c4 + 3]);
                     *reinterpret_cast<float4 *>(cw + kRowOp + off) =
                         make_float4(clo[4 * c4], clo[4 * c4 + 1], clo[4 * c4 + 2], clo[4 * c4 + 3]);
-                    if (pass == 0 && want_dh)
+                    if (kW && want_dh)
                         *reinterpret_cast<float4 *>(cw + 2 * kRowOp + off) =
                             make_float4(whi[4 * c4], whi[4 * c4 + 1], whi[4 * c4 + 2], whi[4 * c4 + 3]);
                 }
-                fence_async_smem();
-                tc_fence_before();
-                mbar_arrive(bar(bCfull + b));
+                tmem_wait_ld();
+                if (part2) {
+#pragma unroll
+                    for (int i = 0; i < kCols; i++) gs[i] += gp[i];
+                }
+                if (more) {
+#pragma unroll
+                    for (int i = 0; i < kCols; i++) zcur[i] = znext[i];
+                }
+                warp_arrive(bar(bCfull + b));
             }
             // pass end: the last one or two partials complete G of this pass
             if (ok && (ok = warp_wait(bar(bGdone), (uint32_t)pass, abort_f, limit))) {
@@ -343,14 +404,14 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     for (int i = 0; i < kCols; i++)
                         xt[i] = d0 + i < D ? x[i] + eps * (gs[i] - x[i] * inv_sp2) + sq * xv[i] : 0.0f;
                     put_row_pair(sm + oVhi, sm + oVlo, r, h, xt);
-                    fence_async_smem();
-                    tc_fence_before();
-                    mbar_arrive(bar(bVready));
+                    warp_arrive(bar(bVready));
 #pragma unroll
                     for (int i = 0; i < kCols; i++) gs[i] = 0.0f;
                 }
             }
-        }
+        };
+        run_pass(PassC<0>{});
+        run_pass(PassC<1>{});
         // gs holds the own dimensions of the G row at x~.  The MH log-ratio (FP64):
         //   ell = [ll(x~) - |x~|^2/2sp2] - [ll(x) - |x|^2/2sp2] - |e|^2/(4 eps) + |xi|^2/2,
         //   e = x - x~ - eps grad log p(x~), summed over the four warpgroups.
@@ -400,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         if (want_dh && ok) {
             // diag(X^T W X) accumulated over the chunks of pass 1 (untouched by pass 2); the
             // condition is warp-uniform, as the collective TMEM load requires
-            tmem_ld8(lrow + 128 + (uint32_t)d0, dh);
+            tmem_ld8(lrow + kColH + (uint32_t)d0, dh);
             tmem_wait_ld();
         }
         if (valid) {
@@ -457,6 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             }
         }
     }
+    __syncwarp();  // the issuer and producer lanes of a warp re-converge here
     tc_fence_before();
     __syncthreads();
     if (warp == kMmaWarp) {

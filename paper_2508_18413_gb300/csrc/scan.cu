@@ -583,7 +583,7 @@ scan_diag_staged_kernel(int T, int D, int TT, const S *__restrict__ a, const S *
     }
     for (int e = (int)(s_bytes / sizeof(R)) + threadIdx.x; e < Ev; e += 256) ss[e] = s[base + e];
     // the copies complete on their own; the bound only guards against a lost completion
-    if (!tc::mbar_wait_drain(mbar, 0, 1u << 24) && threadIdx.x == 0) atomicExch(&ctl->timeout, 1u);
+    if (!tc::mbar_wait_drain(mbar, 0, 1u << 20) && threadIdx.x == 0) atomicExch(&ctl->timeout, 1u);
     __syncthreads();
 
     const bool lane_on = lane < L;
