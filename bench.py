@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--scan-log2", default="20,22,24,26,28",
                     help="scan_sweep: log2 of the element counts T*D")
     ap.add_argument("--scan-d", type=int, default=8, help="scan_sweep: channels D")
+    ap.add_argument("--scan-t", default=None,
+                    help="scan_sweep: comma list of T (overrides --scan-log2)")
     ap.add_argument("--scan-precisions", default="f32,f32_scan_bf16",
                     help="scan_sweep: precisions")
     ap.add_argument("--scan-kernel", choices=["rows", "staged"], default=None,
@@ -558,8 +560,9 @@ def run_other(args):
         peak = _measured_hbm()
         D = args.scan_d
         for prec in args.scan_precisions.split(","):
-            for k in (int(x) for x in args.scan_log2.split(",")):
-                T = (1 << k) // D
+            Ts = ([int(x) for x in args.scan_t.split(",")] if args.scan_t else
+                  [(1 << int(k)) // D for k in args.scan_log2.split(",")])
+            for T in Ts:
                 n = T * D
                 sd = torch.float32
                 ad = torch.bfloat16 if prec == "f32_scan_bf16" else sd

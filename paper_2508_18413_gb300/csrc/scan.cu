@@ -52,6 +52,46 @@ __device__ __forceinline__ void finish_tile(ScanCtl *ctl, unsigned int ntiles) {
     }
 }
 
+// Block-wide reduction of the scan statistics: one atomic per CTA (same-address atomics from
+// every warp of every tile serialise in L2).  Called by all threads of the CTA.
+__device__ __forceinline__ void block_stats(EvalStats *stats, double dmax, unsigned int resets) {
+    __shared__ double s_dm[32];
+    __shared__ unsigned int s_rs[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double dm = warp_max(dmax);
+    unsigned int rs = warp_sum(resets);
+    if (lane == 0) {
+        s_dm[w] = dm;
+        s_rs[w] = rs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < nw; i++) {
+            dm = fmax(dm, s_dm[i]);
+            rs += s_rs[i];
+        }
+        if (dm > 0) atomic_max_d(&stats->dmax, dm);
+        if (rs) atomicAdd(&stats->resets, (unsigned long long)rs);
+    }
+}
+
+// Exit of a persistent scan kernel: every CTA has taken its last (out-of-range) ticket before it
+// counts itself out, so the last CTA to leave can reset the ticket and advance the epoch with
+// no CTA left that could take another ticket.
+__device__ __forceinline__ void exit_persistent(ScanCtl *ctl) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int e = atomicAdd(&ctl->done, 1u);
+        if (e == gridDim.x - 1) {
+            ctl->ticket = 0;
+            ctl->done = 0;
+            ctl->epoch = ctl->epoch + 1u;
+            __threadfence();
+        }
+    }
+}
+
 // Wait (bounded) until tile j's flag carries this epoch; returns the state (0 on timeout).
 __device__ __forceinline__ unsigned int wait_flag(const unsigned int *flags, int j,
                                                   unsigned int epoch, unsigned int limit,
@@ -71,34 +111,59 @@ __device__ __forceinline__ unsigned int make_flag(unsigned int epoch, unsigned i
     return ((epoch & 0x3fffffffu) << 2) | state;
 }
 
-// Warp-parallel look-back for the diagonal scans (warp 0 of the CTA, D <= 32 channels).
-// Lane l examines predecessor tile jend - l; the nearest tile whose inclusive value is
-// published ends the walk; the aggregates of the tiles in between are composed with a
-// shuffle tree per channel (lower lane = later map).  Windows of 32 predecessors are examined
-// at once, so the walk costs one round of loads per 32 tiles.  Returns, in lane d < D, the
-// carry (delta at the end of tile - 1) of channel d.  Waits are bounded; a wait that runs out
-// ends the walk with a zero carry and leaves the timeout flag set.
+// Block-wide look-back over windows of 64 predecessors (all 256 threads, D <= 32 channels).
+// Thread i examines predecessor p = i % 64 of the window for channel group g = i / 64
+// (channels 8g .. 8g + 7), so one round of independent loads brings every channel of the whole
+// window; only the 64 threads of group 0 poll the flags.  The nearest predecessor with a
+// published inclusive value (or tile -1, or a timed-out wait) ends the walk; the aggregates in
+// between are composed per channel by a shuffle tree in each warp (lower lane = nearer, later
+// map) and then across the two warps of the group.  Returns the carry of channel d in shared
+// carry_out[d].
 template <typename R>
-__device__ __forceinline__ R lookback_window(const unsigned int *flags, const R *gagg,
-                                             const R *gincl, int tile, int D,
-                                             unsigned int epoch, unsigned int spin_limit,
-                                             ScanCtl *ctl) {
-    const int lane = threadIdx.x & 31;
-    R MA = R(1), MB = R(0), carry = R(0);
+__device__ void lookback_block64(const unsigned int *flags, const R *gagg, const R *gincl, int tile,
+                                 int D, unsigned int epoch, unsigned int spin_limit, ScanCtl *ctl,
+                                 R *carry_out) {
+    __shared__ int s_k;
+    __shared__ unsigned int s_st[64];
+    __shared__ R s_wa[2][32], s_wb[2][32], s_iv[32], s_MA[32], s_MB[32];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int pj = tid & 63, g = tid >> 6, half = pj >> 5;
+    if (tid < 32) {
+        s_MA[tid] = R(1);
+        s_MB[tid] = R(0);
+    }
     int jend = tile - 1;
     for (;;) {
-        const int j = jend - lane;
-        unsigned int st = kFlagIncl;
-        if (j >= 0) st = wait_flag(flags, j, epoch, spin_limit, ctl);
-        const bool stop = (j < 0) || st != kFlagAgg;  // inclusive, before tile 0, or timeout
-        const unsigned int ball = __ballot_sync(0xffffffffu, stop);
-        const int k = ball ? __ffs(ball) - 1 : 32;
-        for (int d = 0; d < D; d++) {
-            R a = R(1), b = R(0);
-            if (lane < k) {
-                a = gagg[((size_t)j * 2) * D + d];
-                b = gagg[((size_t)j * 2 + 1) * D + d];
+        if (tid == 0) s_k = 64;
+        __syncthreads();
+        const int j = jend - pj;
+        if (g == 0) {
+            unsigned int st = kFlagIncl;
+            if (j >= 0) st = wait_flag(flags, j, epoch, spin_limit, ctl);
+            s_st[pj] = st;
+            if (j < 0 || st != kFlagAgg) atomicMin(&s_k, pj);
+        }
+        __syncthreads();
+        const int k = s_k;
+        const unsigned int st = s_st[pj];
+        if (k < 64 && pj == k) {
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const int d = 8 * g + c;
+                if (d < D) s_iv[d] = (j >= 0 && st == kFlagIncl) ? gincl[(size_t)j * D + d] : R(0);
             }
+        }
+        R ga[8], gb[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const int d = 8 * g + c;
+            const bool on = pj < k && d < D;
+            ga[c] = on ? gagg[((size_t)j * 2) * D + d] : R(1);
+            gb[c] = on ? gagg[((size_t)j * 2 + 1) * D + d] : R(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            R a = ga[c], b = gb[c];
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const R oa = __shfl_down_sync(0xffffffffu, a, off);
@@ -108,106 +173,27 @@ __device__ __forceinline__ R lookback_window(const unsigned int *flags, const R 
                     a = a * oa;
                 }
             }
-            const R Wa = __shfl_sync(0xffffffffu, a, 0), Wb = __shfl_sync(0xffffffffu, b, 0);
-            R iv = R(0);
-            if (k < 32) {
-                R v = R(0);
-                if (lane == k && j >= 0 && st == kFlagIncl) v = gincl[(size_t)j * D + d];
-                iv = __shfl_sync(0xffffffffu, v, k);
-            }
-            if (lane == d) {
-                MB = MA * Wb + MB;
-                MA = MA * Wa;
-                if (k < 32) carry = MA * iv + MB;
-            }
-        }
-        if (k < 32) break;
-        jend -= 32;
-    }
-    return carry;
-}
-
-// Block-wide look-back for the diagonal scans (all 256 threads, D <= 32 channels): thread i
-// examines predecessor tile jend - i, so one round of loads covers 256 tiles.  The nearest
-// tile with a published inclusive value (or tile -1, or a timed-out wait) ends the walk; the
-// aggregates of the tiles in between are composed per channel, first within each warp by a
-// shuffle tree (lower lane = later map), then across the 8 warps in order.  Returns the carry
-// of channel d in shared carry_out[d].
-template <typename R>
-__device__ void lookback_block(const unsigned int *flags, const R *gagg, const R *gincl, int tile,
-                               int D, unsigned int epoch, unsigned int spin_limit, ScanCtl *ctl,
-                               R *carry_out) {
-    __shared__ int s_k;
-    __shared__ R s_wa[8][32], s_wb[8][32], s_iv[32], s_MA[32], s_MB[32];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid < 32) {
-        s_MA[tid] = R(1);
-        s_MB[tid] = R(0);
-    }
-    int jend = tile - 1;
-    for (;;) {
-        if (tid == 0) s_k = 256;
-        __syncthreads();
-        const int j = jend - tid;
-        unsigned int st = kFlagIncl;
-        if (j >= 0) st = wait_flag(flags, j, epoch, spin_limit, ctl);
-        const bool stop = (j < 0) || st != kFlagAgg;
-        if (stop) atomicMin(&s_k, tid);
-        __syncthreads();
-        const int k = s_k;
-        if (tid == k && k < 256)
-            for (int d = 0; d < D; d++) s_iv[d] = (j >= 0 && st == kFlagIncl) ? gincl[(size_t)j * D + d] : R(0);
-        // channels in batches of 8: all 16 loads of a batch are in flight together
-        for (int d0 = 0; d0 < D; d0 += 8) {
-            R ga[8], gb[8];
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                ga[c] = R(1);
-                gb[c] = R(0);
-                if (tid < k && d0 + c < D) {
-                    ga[c] = gagg[((size_t)j * 2) * D + d0 + c];
-                    gb[c] = gagg[((size_t)j * 2 + 1) * D + d0 + c];
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                R a = ga[c], b = gb[c];
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const R oa = __shfl_down_sync(0xffffffffu, a, off);
-                    const R ob = __shfl_down_sync(0xffffffffu, b, off);
-                    if (lane + off < 32) {
-                        b = a * ob + b;
-                        a = a * oa;
-                    }
-                }
-                if (lane == 0 && d0 + c < D) {
-                    s_wa[w][d0 + c] = a;
-                    s_wb[w][d0 + c] = b;
-                }
+            const int d = 8 * g + c;
+            if (lane == 0 && d < D) {
+                s_wa[half][d] = a;
+                s_wb[half][d] = b;
             }
         }
         __syncthreads();
         if (tid < D) {
-            // window map W = warp 0 o warp 1 o ... o warp 7 (warp 0 is the nearest = latest)
-            R Wa = R(1), Wb = R(0);
-            for (int q = 7; q >= 0; q--) {  // compose from the farthest to the nearest
-                const R qa = s_wa[q][tid], qb = s_wb[q][tid];
-                Wb = qa * Wb + qb;
-                Wa = qa * Wa;
-            }
-            // M <- M o W
-            const R MA = s_MA[tid], MB = s_MB[tid];
+            // window map W = half 0 o half 1 (half 0 holds the nearer predecessors)
+            const R Wb = s_wa[0][tid] * s_wb[1][tid] + s_wb[0][tid];
+            const R Wa = s_wa[0][tid] * s_wa[1][tid];
+            const R MA = s_MA[tid], MB = s_MB[tid];  // M <- M o W
             s_MB[tid] = MA * Wb + MB;
             s_MA[tid] = MA * Wa;
-            if (k < 256) carry_out[tid] = s_MA[tid] * s_iv[tid] + s_MB[tid];
+            if (k < 64) carry_out[tid] = s_MA[tid] * s_iv[tid] + s_MB[tid];
         }
         __syncthreads();
-        if (k < 256) break;
-        jend -= 256;
+        if (k < 64) break;
+        jend -= 64;
     }
 }
-
 }  // namespace
 
 // ==========================================================================================
@@ -352,14 +338,7 @@ scan_diag_kernel(int T, int D, int TT, const S *__restrict__ a, const S *__restr
     __syncthreads();
     for (int e = tid; e < Ev; e += kScanThreads) s[base + e] = ss[smem_idx(e)];
 
-    if (stats) {
-        double dm = warp_max((double)dmax);
-        unsigned int rs = warp_sum(resets);
-        if ((tid & 31) == 0) {
-            if (dm > 0) atomic_max_d(&stats->dmax, dm);
-            if (rs) atomicAdd(&stats->resets, (unsigned long long)rs);
-        }
-    }
+    if (stats) block_stats(stats, (double)dmax, resets);
     finish_tile(ctl, ntiles);
 }
 
@@ -389,12 +368,17 @@ scan_diag_rows_kernel(int T, int D, int NSUB, const S *__restrict__ a, const S *
     const int WT = NSUB * ROWS * P;      // timesteps per warp (a contiguous chunk)
     const int TT = 8 * WT;
     const unsigned int ntiles = (unsigned int)ceil_div(T, TT);
-    const int tile = (int)take_tile(ctl, &s_tile, &s_epoch);
-    const unsigned int epoch = s_epoch;
     const bool lane_on = lane < L;
     const int d = lane_on ? lane % D : 0;
     const int tsub = lane_on ? lane / D : 0;
     const int last_lane = (P - 1) * D + d;  // lane holding the row end of channel d
+    R dmax = R(0);
+    unsigned int resets = 0;
+    // persistent: the CTA takes tiles in ticket order until they run out
+    for (;;) {
+    const int tile = (int)take_tile(ctl, &s_tile, &s_epoch);
+    if (tile >= (int)ntiles) break;
+    const unsigned int epoch = s_epoch;
     const long long t_warp = (long long)tile * TT + (long long)w * WT;
 
     // pass 1: the warp aggregate over its chunk (a, b only)
@@ -454,7 +438,7 @@ scan_diag_rows_kernel(int T, int D, int NSUB, const S *__restrict__ a, const S *
     __syncthreads();
     if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
     if (tile > 0) {
-        lookback_block<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
+        lookback_block64<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
         if (threadIdx.x < D) {
             gincl[(size_t)tile * D + threadIdx.x] = tA[threadIdx.x] * ccar[threadIdx.x] + tB[threadIdx.x];
             __threadfence();
@@ -475,8 +459,6 @@ scan_diag_rows_kernel(int T, int D, int NSUB, const S *__restrict__ a, const S *
     __syncthreads();
     // pass 2: re-read the chunk (a, b from L2), apply rows in order from the carry
     R delta = lane_on ? cin[w][d] : R(0);
-    R dmax = R(0);
-    unsigned int resets = 0;
     for (int sub = 0; sub < NSUB; sub++) {
         const long long t_base = t_warp + (long long)sub * ROWS * P;
         R ra[ROWS], rb[ROWS], rs[ROWS];
@@ -515,14 +497,138 @@ scan_diag_rows_kernel(int T, int D, int NSUB, const S *__restrict__ a, const S *
             delta = __shfl_sync(0xffffffffu, dl, last_lane);
         }
     }
-    if (stats) {
-        double dm = warp_max((double)dmax);
-        unsigned int rsum = warp_sum(resets);
-        if (lane == 0) {
-            if (dm > 0) atomic_max_d(&stats->dmax, dm);
-            if (rsum) atomicAdd(&stats->resets, (unsigned long long)rsum);
+    __syncthreads();  // shared arrays are reused by the next tile
+    }
+    if (stats) block_stats(stats, (double)dmax, resets);
+    exit_persistent(ctl);
+}
+
+// ==========================================================================================
+// Diagonal scan, D <= 32, one register-resident sub-chunk per warp: each lane loads its ROWS
+// (a, b, s) elements once, scans its rows in place, and keeps the row prefixes in registers
+// through the look-back, so every element crosses HBM exactly once (read a, b, s; write s).
+// Small tiles (8 ROWS P timesteps) keep many CTAs resident, which hides the look-back latency.
+// ==========================================================================================
+template <typename R, typename S, int ROWS>
+__global__ void __launch_bounds__(256, (ROWS > 8 || sizeof(R) == 8) ? 2 : 4)
+scan_diag_reg_kernel(int T, int D, const S *__restrict__ a, const S *__restrict__ b,
+                     R *__restrict__ s, const R *__restrict__ s_reset, unsigned int *flags,
+                     R *__restrict__ gagg, R *__restrict__ gincl, ScanCtl *ctl, EvalStats *stats,
+                     const int *skip, unsigned int spin_limit) {
+    if (skip && *(volatile const int *)skip) return;
+    __shared__ unsigned int s_tile, s_epoch;
+    __shared__ R wA[8][32], wB[8][32];   // warp aggregates per channel
+    __shared__ R cin[8][32];             // carry into each warp
+    __shared__ R tA[32], tB[32], ccar[32];
+    const int P = 32 / D, L = P * D;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int WT = ROWS * P;             // timesteps per warp
+    const int TT = 8 * WT;
+    const unsigned int ntiles = (unsigned int)ceil_div(T, TT);
+    const int tile = (int)take_tile(ctl, &s_tile, &s_epoch);
+    const unsigned int epoch = s_epoch;
+    const bool lane_on = lane < L;
+    const int d = lane_on ? lane % D : 0;
+    const int tsub = lane_on ? lane / D : 0;
+    const int last_lane = (P - 1) * D + d;
+    const long long t_base = (long long)tile * TT + (long long)w * WT;
+
+    R ra[ROWS], rb[ROWS], rs[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        const long long t = t_base + (long long)r * P + tsub;
+        const bool in = lane_on && t < T;
+        const size_t e = (size_t)t * D + d;
+        ra[r] = in ? ldg_as<S, R>(a + e) : R(1);
+        rb[r] = in ? ldg_as<S, R>(b + e) : R(0);
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {  // s is only needed after the look-back
+        const long long t = t_base + (long long)r * P + tsub;
+        rs[r] = (lane_on && t < T) ? __ldcs(s + (size_t)t * D + d) : R(0);
+    }
+    R WA = R(1), WB = R(0);
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        for (int off = D; off < L; off <<= 1) {
+            const R pa = __shfl_up_sync(0xffffffffu, ra[r], off);
+            const R pb = __shfl_up_sync(0xffffffffu, rb[r], off);
+            if (lane_on && lane >= off) {
+                rb[r] = ra[r] * pb + rb[r];
+                ra[r] = ra[r] * pa;
+            }
+        }
+        const R ea = __shfl_sync(0xffffffffu, ra[r], last_lane);
+        const R eb = __shfl_sync(0xffffffffu, rb[r], last_lane);
+        WB = ea * WB + eb;
+        WA = ea * WA;
+    }
+    if (lane < D) {
+        wA[w][lane] = WA;
+        wB[w][lane] = WB;
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        const int dd = threadIdx.x;
+        R TA_ = R(1), TB_ = R(0);
+        for (int q = 0; q < 8; q++) {
+            TB_ = wA[q][dd] * TB_ + wB[q][dd];
+            TA_ = wA[q][dd] * TA_;
+        }
+        tA[dd] = TA_;
+        tB[dd] = TB_;
+        if (tile == 0) {
+            gincl[dd] = TB_;
+        } else {
+            gagg[((size_t)tile * 2) * D + dd] = TA_;
+            gagg[((size_t)tile * 2 + 1) * D + dd] = TB_;
+        }
+        ccar[dd] = R(0);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
+    if (tile > 0) {
+        lookback_block64<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
+        if (threadIdx.x < D) {
+            gincl[(size_t)tile * D + threadIdx.x] = tA[threadIdx.x] * ccar[threadIdx.x] + tB[threadIdx.x];
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, kFlagIncl));
+    }
+    if (threadIdx.x < D) {
+        const int dd = threadIdx.x;
+        R pa = R(1), pb = R(0);
+        const R c = ccar[dd];
+        for (int q = 0; q < 8; q++) {
+            cin[q][dd] = pa * c + pb;
+            pb = wA[q][dd] * pb + wB[q][dd];
+            pa = wA[q][dd] * pa;
         }
     }
+    __syncthreads();
+    // rows in order from the carry, from the prefixes held in registers
+    R delta = lane_on ? cin[w][d] : R(0);
+    R dmax = R(0);
+    unsigned int resets = 0;
+#pragma unroll
+    for (int r = 0; r < ROWS; r++) {
+        const R dl = ra[r] * delta + rb[r];
+        const long long t = t_base + (long long)r * P + tsub;
+        if (lane_on && t < T) {
+            R sn = rs[r] + dl;
+            if (!finite(sn)) {
+                sn = s_reset ? s_reset[d] : R(0);
+                resets++;
+            } else {
+                dmax = max(dmax, fabs(dl));
+            }
+            __stcs(s + (size_t)t * D + d, sn);
+        }
+        delta = __shfl_sync(0xffffffffu, dl, last_lane);
+    }
+    if (stats) block_stats(stats, (double)dmax, resets);
     finish_tile(ctl, ntiles);
 }
 
@@ -640,7 +746,7 @@ scan_diag_staged_kernel(int T, int D, int TT, const S *__restrict__ a, const S *
     __syncthreads();
     if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
     if (tile > 0) {
-        lookback_block<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
+        lookback_block64<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
         if (threadIdx.x < D) {
             gincl[(size_t)tile * D + threadIdx.x] = tA[threadIdx.x] * ccar[threadIdx.x] + tB[threadIdx.x];
             __threadfence();
@@ -691,14 +797,7 @@ scan_diag_staged_kernel(int T, int D, int TT, const S *__restrict__ a, const S *
         }
         delta = __shfl_sync(0xffffffffu, dl, last_lane);
     }
-    if (stats) {
-        double dm = warp_max((double)dmax);
-        unsigned int rsum = warp_sum(resets);
-        if (lane == 0) {
-            if (dm > 0) atomic_max_d(&stats->dmax, dm);
-            if (rsum) atomicAdd(&stats->resets, (unsigned long long)rsum);
-        }
-    }
+    if (stats) block_stats(stats, (double)dmax, resets);
     finish_tile(ctl, ntiles);
 }
 
@@ -806,6 +905,29 @@ static void diag_shape(int T, int D, int *rows, int *nsub) {
     }
 }
 
+// CTAs of `kernel` (block of `threads`, no dynamic shared memory) resident on the device at
+// once, cached per kernel.
+template <class K>
+static int resident_ctas(K kernel, int threads) {
+    static const void *keys[16] = {};
+    static int vals[16] = {};
+    static int n = 0;
+    const void *key = reinterpret_cast<const void *>(kernel);
+    for (int i = 0; i < n; i++)
+        if (keys[i] == key) return vals[i];
+    int per_sm = 1, dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int v = per_sm * sms;
+    if (n < 16) {
+        keys[n] = key;
+        vals[n++] = v;
+    }
+    return v;
+}
+
 template <typename R, typename S>
 static cudaError_t run_scan_rows(int T, int D, const void *a, const void *b, void *s,
                                  const void *s_reset, const ScanWork &w, EvalStats *stats,
@@ -814,14 +936,31 @@ static cudaError_t run_scan_rows(int T, int D, const void *a, const void *b, voi
     diag_shape(T, D, &rows, &nsub);
     const int ntiles = ceil_div(T, 8 * rows * nsub * (32 / D));
     if (ntiles > w.max_tiles) return cudaErrorInvalidValue;
+    if (nsub == 1) {  // one sub-chunk: the register-resident single-read kernel
+        if (rows == 16) {
+            prefer_shared(scan_diag_reg_kernel<R, S, 16>);
+            scan_diag_reg_kernel<R, S, 16><<<ntiles, 256, 0, st>>>(
+                T, D, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags, (R *)w.agg,
+                (R *)w.incl, w.ctl, stats, skip, spin);
+        } else {
+            prefer_shared(scan_diag_reg_kernel<R, S, 8>);
+            scan_diag_reg_kernel<R, S, 8><<<ntiles, 256, 0, st>>>(
+                T, D, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags, (R *)w.agg,
+                (R *)w.incl, w.ctl, stats, skip, spin);
+        }
+        return cudaGetLastError();
+    }
+    // persistent grid: at most the CTAs that can be resident at once
     if (rows == 16) {
-        prefer_shared(scan_diag_rows_kernel<R, S, 16>);
-        scan_diag_rows_kernel<R, S, 16><<<ntiles, 256, 0, st>>>(
+        auto k = scan_diag_rows_kernel<R, S, 16>;
+        prefer_shared(k);
+        k<<<std::min(ntiles, resident_ctas(k, 256)), 256, 0, st>>>(
             T, D, nsub, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags,
             (R *)w.agg, (R *)w.incl, w.ctl, stats, skip, spin);
     } else {
-        prefer_shared(scan_diag_rows_kernel<R, S, 8>);
-        scan_diag_rows_kernel<R, S, 8><<<ntiles, 256, 0, st>>>(
+        auto k = scan_diag_rows_kernel<R, S, 8>;
+        prefer_shared(k);
+        k<<<std::min(ntiles, resident_ctas(k, 256)), 256, 0, st>>>(
             T, D, nsub, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags,
             (R *)w.agg, (R *)w.incl, w.ctl, stats, skip, spin);
     }
@@ -1171,14 +1310,7 @@ scan_dense_small_kernel(int T, int D, const R *__restrict__ a, const R *__restri
             s[(size_t)t * D + i] = sn;
         }
     }
-    if (stats) {
-        double dm = warp_max((double)dmax);
-        unsigned int rs = warp_sum(resets);
-        if (lane == 0) {
-            if (dm > 0) atomic_max_d(&stats->dmax, dm);
-            if (rs) atomicAdd(&stats->resets, (unsigned long long)rs);
-        }
-    }
+    if (stats) block_stats(stats, (double)dmax, resets);
     finish_tile(ctl, ntiles);
 }
 
