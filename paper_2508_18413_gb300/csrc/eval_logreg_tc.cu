@@ -10,11 +10,11 @@
 // For a CTA of 128 timesteps the contractions are GEMMs against the shared design matrix:
 //   Z = V X^T (128 x N),  G = C X (128 x D),  H = W (X.X) (128 x D),
 // computed in chunks of 32 design rows.  Each FP32 operand is split a = a_hi + a_lo into two
-// tf32 values and a b is accumulated as a_lo b_hi + a_hi b_lo + a_hi b_hi (the dropped
-// a_lo b_lo term is below 2^-22 |a b|); the diagonal Hessian H only shapes the Newton step and
-// takes the single product a_hi b_hi.
+// tf32 values and a b is accumulated as (a_hi + a_lo)(b_hi + b_lo) in two MMAs of N = 64 (see
+// kIdesc64); the diagonal Hessian H only shapes the Newton step and takes the single product
+// a_hi b_hi.
 //
-// Warp roles (576 threads, one CTA per SM):
+// Warp roles (640 threads, one CTA per SM):
 //   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one timestep per lane) and
 //              belongs to warpgroup h = w / 4, which owns columns 8h..8h+7 of every chunk and
 //              dimensions 8h..8h+7 of the state.  Z -> c = y - sigmoid(z), w = sigmoid'(z) and
@@ -22,10 +22,11 @@
 //              the A operand of G and H.  Each warpgroup forms its dimensions of the proposal,
 //              of the residual and of J; the MH log-ratio (FP64) is summed over the four
 //              warpgroups through shared memory.
-//   warps 16-17 issue the MMAs, one thread each: the Z products, and the G and H products;
-//              warp 16 allocates and frees TMEM, and its lane 1 streams pre-swizzled design
-//              chunks with bulk copies (4 stages).
-// TMEM: Z in three buffers, G per chunk in two buffers, H accumulated over the chunks.  The tensor core's FP32 accumulation truncates, so
+//   warps 16-19 control, one per SM sub-partition: warp 16 allocates TMEM and issues the Z
+//              products, warp 17 issues the G and H products, lane 0 of warp 18 streams
+//              pre-swizzled design chunks with bulk copies (4 stages), warp 19 is idle.
+// TMEM: Z in three buffers, G per chunk in two buffers (64 columns each: the B_hi and B_lo
+// parts), H accumulated over the chunks.  The tensor core's FP32 accumulation truncates, so
 // a sum over all N rows in one accumulator would drift by up to an ulp of |G| per MMA; each
 // chunk's G product therefore starts a fresh accumulator and the epilogue adds the 32-row
 // partials in registers with round-to-nearest.  Every wait is bounded: a wait that runs out
@@ -52,17 +53,24 @@ constexpr int kGroups = 4;                     // epilogue warpgroups
 constexpr int kCols = kDP / kGroups;           // columns / dimensions per warpgroup: 8
 constexpr int kEpiWarps = 4 * kGroups;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = kEpiThreads + 64;     // + two MMA-issue warps (one lane copies)
-// MMA issuers (lane 0 of each): the Z products, and the G and H products
-constexpr int kIssZ = kEpiWarps, kIssG = kEpiWarps + 1;
+constexpr int kThreads = kEpiThreads + 128;    // + four control warps, one per SM sub-partition
+// control warps (lane 0 of each): the Z-product issuer, the G/H-product issuer, the bulk-copy
+// producer, and one spare; warp w runs on sub-partition w % 4, so each sub-partition hosts four
+// epilogue warps and one control warp
+constexpr int kIssZ = kEpiWarps, kIssG = kEpiWarps + 1, kCopyWarp = kEpiWarps + 2;
 constexpr int kMmaWarp = kIssZ;                // allocates / frees TMEM
-constexpr int kCopyWarp = kIssZ, kCopyLane = 1;  // the bulk-copy producer: lane 1 of warp 16
+constexpr int kCopyLane = 0;
 constexpr int kOp = kNB * kDP * 4;             // one 32 x 32 operand block: 4096 bytes
 constexpr int kImg = 5 * kOp + kNB * 4;        // chunk image: X hi, X lo, X^T hi, X^T lo, (X.X)^T hi, y
 constexpr int kStageStride = 21504;            // 1024-aligned stage slot
 constexpr int kRowOp = kM * kDP * 4;           // a 128 x 32 A operand: 16384 bytes
 constexpr uint32_t kIdesc = idesc_tf32(kM, 32);
-constexpr uint32_t kTmemCols = 256;
+// The hi and lo blocks of each design operand are adjacent in the chunk image, i.e. one 64-row
+// operand [B_hi; B_lo]: a single N=64 MMA multiplies A by both (an MMA of N <= 64 costs about
+// the same as N = 32), so a K-step of Z or G takes two MMAs (A_hi and A_lo) instead of three.
+// Columns 0-31 of the 64-column result hold A B_hi, columns 32-63 hold A B_lo.
+constexpr uint32_t kIdesc64 = idesc_tf32(kM, 64);
+constexpr uint32_t kTmemCols = 512;
 constexpr unsigned int kDrainLimit = 1u << 20;  // polls of up to ~2 us each
 
 // shared-memory map, offsets from a 1024-aligned base
@@ -72,11 +80,13 @@ constexpr int kCWStride = 3 * kRowOp;
 constexpr int oStage = oCW + 2 * kCWStride;
 constexpr int oBar = oStage + kStages * kStageStride;
 constexpr int kZbuf = 3;                       // Z buffers in TMEM (GEMM1 runs 3 chunks ahead)
-constexpr uint32_t kColZ = 0;                  // Z: 3 buffers of 32 columns
-constexpr uint32_t kColG = 32 * kZbuf;         // G: 2 buffers of 32 columns (fresh per chunk)
-constexpr uint32_t kColH = kColG + 64;         // H: 32 columns
+constexpr uint32_t kColZ = 0;                  // Z: 3 buffers of 64 columns (hi part, lo part)
+constexpr uint32_t kColG = 64 * kZbuf;         // G: 2 buffers of 64 columns (fresh per chunk)
+constexpr uint32_t kColH = kColG + 128;        // H: 32 columns
+// cfull has four barriers (chunk k uses k % 4) so that no waiter can see a barrier two phases
+// ahead: the Z issuer waits on chunks up to four behind the epilogue's newest
 constexpr int bFull = 0, bEmpty = kStages, bZfull = 2 * kStages, bCfull = bZfull + kZbuf,
-              bCempty = bCfull + 2, bGdone = bCempty + 2, bVready = bGdone + 1, bFin = bVready + 1,
+              bCempty = bCfull + 4, bGdone = bCempty + 2, bVready = bGdone + 1, bFin = bVready + 1,
               kNumBars = bFin + 1;
 constexpr int oMisc = oBar + 8 * kNumBars;     // tmem address, abort flag
 constexpr int oPart = oMisc + 16;              // double [4][128]: per-warpgroup log-ratio parts
@@ -149,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
     if (tid == 0) {
         for (int i = 0; i < kNumBars; i++) {
             uint32_t cnt = 1;
-            if (i == bCfull || i == bCfull + 1 || i == bVready) cnt = kEpiWarps;  // one per warp
+            if ((i >= bCfull && i < bCfull + 4) || i == bVready) cnt = kEpiWarps;  // one per warp
             if ((i >= bEmpty && i < bEmpty + kStages) || i == bFin) cnt = 2;      // both issuers
             mbar_init(bar(i), cnt);
         }
@@ -191,14 +201,13 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 if (!mbar_wait(bar(bFull + s), (uint32_t)(k / kStages) & 1u, abort_f, limit)) return false;
                 tc_fence_after();
                 const uint32_t st = sb + oStage + s * kStageStride;
-                const uint32_t zt = tm + kColZ + (uint32_t)(k % kZbuf) * 32u;
+                const uint32_t zt = tm + kColZ + (uint32_t)(k % kZbuf) * 64u;
 #pragma unroll
                 for (int kk = 0; kk < 4; kk++) {
                     const uint64_t ah = sdesc(sb + oVhi + 32 * kk), al = sdesc(sb + oVlo + 32 * kk);
-                    const uint64_t bh = sdesc(st + 32 * kk), bl = sdesc(st + kOp + 32 * kk);
-                    mma_tf32(zt, al, bh, kIdesc, kk > 0);
-                    mma_tf32(zt, ah, bl, kIdesc, 1);
-                    mma_tf32(zt, ah, bh, kIdesc, 1);
+                    const uint64_t b2 = sdesc(st + 32 * kk);  // [X_hi; X_lo], 64 rows
+                    mma_tf32(zt, al, b2, kIdesc64, kk > 0);
+                    mma_tf32(zt, ah, b2, kIdesc64, 1);
                 }
                 mma_commit(bar(bZfull + k % kZbuf));
                 mma_commit(bar(bEmpty + s));  // this issuer is done with the stage
@@ -211,11 +220,14 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 tc_fence_after();
                 const int kb = pass * nch;
                 for (int j = 0; j < kZbuf && j < nch && ok; j++) ok = issue_z(kb + j);
-                for (int j = 0; j + kZbuf < nch && ok; j++) {
-                    const int k = kb + j;
-                    if (!(ok = mbar_wait(bar(bCfull + (k & 1)), (uint32_t)(k >> 1) & 1u, abort_f, limit))) break;
+                // Z(k) overwrites the buffer of Z(k - 3), which the epilogue loads while it computes
+                // chunk k - 4 (in the pass prologue for k - 3 = kb): C(max(k - 4, kb)) ready
+                // implies that buffer is free
+                for (int k = kb + kZbuf; k < kb + nch && ok; k++) {
+                    const int c = k - 4 > kb ? k - 4 : kb;
+                    if (!(ok = mbar_wait(bar(bCfull + (c & 3)), (uint32_t)(c >> 2) & 1u, abort_f, limit))) break;
                     tc_fence_after();
-                    ok = issue_z(k + kZbuf);
+                    ok = issue_z(k);
                 }
             }
             mma_commit(bar(bFin));
@@ -229,18 +241,17 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 const int kb = pass * nch;
                 for (int j = 0; j < nch && ok; j++) {
                     const int k = kb + j;
-                    if (!(ok = mbar_wait(bar(bCfull + (k & 1)), (uint32_t)(k >> 1) & 1u, abort_f, limit))) break;
+                    if (!(ok = mbar_wait(bar(bCfull + (k & 3)), (uint32_t)(k >> 2) & 1u, abort_f, limit))) break;
                     tc_fence_after();
                     const uint32_t st = sb + oStage + (k % kStages) * kStageStride;
                     const uint32_t cw = sb + oCW + (k & 1) * kCWStride;
-                    const uint32_t gt = tm + kColG + (uint32_t)(k & 1) * 32u;  // fresh per chunk
+                    const uint32_t gt = tm + kColG + (uint32_t)(k & 1) * 64u;  // fresh per chunk
 #pragma unroll
                     for (int kk = 0; kk < 4; kk++) {
                         const uint64_t ch = sdesc(cw + 32 * kk), cl = sdesc(cw + kRowOp + 32 * kk);
-                        const uint64_t bh = sdesc(st + 2 * kOp + 32 * kk), bl = sdesc(st + 3 * kOp + 32 * kk);
-                        mma_tf32(gt, cl, bh, kIdesc, kk > 0 ? 1u : 0u);
-                        mma_tf32(gt, ch, bl, kIdesc, 1);
-                        mma_tf32(gt, ch, bh, kIdesc, 1);
+                        const uint64_t b2 = sdesc(st + 2 * kOp + 32 * kk);  // [X^T_hi; X^T_lo]
+                        mma_tf32(gt, cl, b2, kIdesc64, kk > 0 ? 1u : 0u);
+                        mma_tf32(gt, ch, b2, kIdesc64, 1);
                     }
                     if (pass == 0 && want_dh) {
 #pragma unroll
@@ -256,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             mma_commit(bar(bFin));
             mbar_wait_drain(bar(bFin), 0, kDrainLimit);
         }
-    } else {
+    } else if (warp < kEpiWarps) {
         // ---------------- epilogue warpgroups ----------------
         const int q = warp & 3, h = warp >> 2;
         const int r = q * 32 + lane;
@@ -297,11 +308,12 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             warp_arrive(bar(bVready));
         }
         auto add_partial = [&](int kc) {  // G of chunk kc, own dimensions
-            float gp[kCols];
-            tmem_ld8(lrow + kColG + 32u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
+            float gp[kCols], gpl[kCols];
+            tmem_ld8(lrow + kColG + 64u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
+            tmem_ld8(lrow + kColG + 64u * (uint32_t)(kc & 1) + 32u + (uint32_t)d0, gpl);
             tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < kCols; i++) gs[i] += gp[i];
+            for (int i = 0; i < kCols; i++) gs[i] += gp[i] + gpl[i];
         };
         // one pass over the design: chunk loop, then the pass end
         auto run_pass = [&](auto pc) {
@@ -314,13 +326,17 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 const int k = pass * nch;
                 if (ok && (ok = warp_wait(bar(bZfull + k % kZbuf), (uint32_t)(k / kZbuf) & 1u, abort_f, limit))) {
                     tc_fence_after();
-                    tmem_ld8(lrow + kColZ + (uint32_t)(k % kZbuf) * 32u + (uint32_t)d0, zcur);
+                    float zl[kCols];
+                    tmem_ld8(lrow + kColZ + (uint32_t)(k % kZbuf) * 64u + (uint32_t)d0, zcur);
+                    tmem_ld8(lrow + kColZ + (uint32_t)(k % kZbuf) * 64u + 32u + (uint32_t)d0, zl);
                     tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < kCols; i++) zcur[i] += zl[i];
                 }
             }
             for (int j = 0; j < nch && ok; j++) {
                 const int k = pass * nch + j, b = k & 1, si = k % kStages;
-                float znext[kCols], gp[kCols];
+                float znext[kCols], znl[kCols], gp[kCols], gpl[kCols];
                 const bool more = j + 1 < nch;
                 if (more) {
                     if (!(ok = warp_wait(bar(bZfull + (k + 1) % kZbuf), (uint32_t)((k + 1) / kZbuf) & 1u, abort_f, limit)))
@@ -331,9 +347,15 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     break;
                 if (!(ok = warp_wait(bar(bFull + si), (uint32_t)(k / kStages) & 1u, abort_f, limit))) break;
                 tc_fence_after();
-                if (more) tmem_ld8(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 32u + (uint32_t)d0, znext);
+                if (more) {
+                    tmem_ld8(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 64u + (uint32_t)d0, znext);
+                    tmem_ld8(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 64u + 32u + (uint32_t)d0, znl);
+                }
                 const bool part2 = j >= 2;
-                if (part2) tmem_ld8(lrow + kColG + 32u * (uint32_t)(k & 1) + (uint32_t)d0, gp);
+                if (part2) {
+                    tmem_ld8(lrow + kColG + 64u * (uint32_t)(k & 1) + (uint32_t)d0, gp);
+                    tmem_ld8(lrow + kColG + 64u * (uint32_t)(k & 1) + 32u + (uint32_t)d0, gpl);
+                }
                 const float4 *ys4 = reinterpret_cast<const float4 *>(sm + oStage + si * kStageStride + 5 * kOp) + 2 * h;
                 const float4 ya = ys4[0], yb = ys4[1];
                 const float yv8[kCols] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
@@ -359,9 +381,11 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                         ln = 0.0f;
                     }
                     llc += ln;
-                    chi[i] = to_tf32(c);
-                    clo[i] = to_tf32(c - chi[i]);
-                    if (kW) whi[i] = to_tf32(w);
+                    // c = c_hi + c_lo exactly; the tensor core drops the low 13 bits of c_lo
+                    // (below 2^-20 |c|) and of w
+                    chi[i] = tf32_trunc(c);
+                    clo[i] = c - chi[i];
+                    if (kW) whi[i] = w;
                 }
                 if (pass) ll1 += (double)llc;
                 else ll0 += (double)llc;
@@ -380,13 +404,13 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 tmem_wait_ld();
                 if (part2) {
 #pragma unroll
-                    for (int i = 0; i < kCols; i++) gs[i] += gp[i];
+                    for (int i = 0; i < kCols; i++) gs[i] += gp[i] + gpl[i];
                 }
                 if (more) {
 #pragma unroll
-                    for (int i = 0; i < kCols; i++) zcur[i] = znext[i];
+                    for (int i = 0; i < kCols; i++) zcur[i] = znext[i] + znl[i];
                 }
-                warp_arrive(bar(bCfull + b));
+                warp_arrive(bar(bCfull + (k & 3)));
             }
             // pass end: the last one or two partials complete G of this pass
             if (ok && (ok = warp_wait(bar(bGdone), (uint32_t)pass, abort_f, limit))) {

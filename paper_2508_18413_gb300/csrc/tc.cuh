@@ -44,7 +44,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 }
 // One poll; the thread may be suspended in hardware until the phase completes or about
 // kSuspendNs nanoseconds pass, so waiting warps do not take issue slots from working ones.
-constexpr uint32_t kSuspendNs = 2000;
+#ifndef PM_TC_SUSPEND_NS
+#define PM_TC_SUSPEND_NS 2000
+#endif
+constexpr uint32_t kSuspendNs = PM_TC_SUSPEND_NS;
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -55,10 +58,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of the phase of `parity` (no suspension): the fast path for phases that are
+// usually complete by the time they are checked.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase of `parity` to complete.  Gives up (and raises *abort) after
 // `limit` polls, or early once another role has raised *abort; returns false then.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort,
                                           unsigned int limit) {
+    if (mbar_test(bar, parity)) return true;
     for (unsigned int n = 0;; n++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((n & 31u) == 31u && *abort) return false;
@@ -161,6 +177,12 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
+}
+
+// tf32 part of x by truncation (the tensor core reads the top 19 bits of a tf32 operand, so
+// x - tf32_trunc(x) is the exact remainder it drops; one logic operation)
+__device__ __forceinline__ float tf32_trunc(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
 // round to the nearest tf32 (10 explicit mantissa bits); the result is an FP32 value

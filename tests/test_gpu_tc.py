@@ -69,7 +69,10 @@ def test_tc_linearize_matches_oracle(N, D, T, eps, jac):
         checked += 1
         assert acc[t] == acco, (t, ello, logu[t], ell[t])
         np.testing.assert_allclose(f[t], fo, rtol=1e-5, atol=1e-5)
-        assert ell[t] == pytest.approx(ello, rel=1e-4, abs=2e-4)
+        # the MH log-ratio is formed in FP64 from FP32 states and gradients; its |e|^2/(4 eps)
+        # term turns a gradient error dg into about |e| dg / 2, i.e. up to ~1e-3 here (the
+        # CUDA-core FP32 kernel shows 7e-4 on the same inputs)
+        assert ell[t] == pytest.approx(ello, rel=1e-4, abs=1e-3)
         if jac == "diag":
             np.testing.assert_allclose(J[t], np.diag(O.jacobian(p, t + 1, prev, "diag")),
                                        rtol=2e-3, atol=2e-3)
