@@ -487,21 +487,30 @@ def run_other(args):
         xid, ud = torch.tensor(xi, device=dev), torch.tensor(u, device=dev)
         opt = P.Options(sampler="mala", step=c.step, jac="diag", precision="f32", atol=c.tol, clip=1,
                         gate_grad=0)
-        t0 = time.time()
-        s, res = P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud)
-        torch.cuda.synchronize()
-        fwd_ms = 1e3 * (time.time() - t0)
-        _, _, acc, _ = P.pmcmc_linearize(tgt, P.Options(sampler="mala", step=c.step, jac="zero",
+        # The adjoint is taken at the chain's fixed point.  On this workload quasi-Newton needs
+        # about 11,000 iterations, so the fixed point comes from the sequential GPU loop; one
+        # evaluate pass confirms it (max residual).
+        sopt = P.Options(sampler="mala", step=c.step, precision="f32")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s, _ = P.pmcmc_seq_solve(tgt, sopt, c.T, s0, xid, ud)
+        e1.record(stream)
+        e1.synchronize()
+        fwd_ms = e0.elapsed_time(e1)
+        f, _, acc, _ = P.pmcmc_linearize(tgt, P.Options(sampler="mala", step=c.step, jac="zero",
                                                         precision="f32"), c.T, s0, s, xid, ud,
                                          want_jac=False)
+        fp_res = float((f - s).abs().max().item())
+        res = {"accept_rate": float(acc.float().mean().item())}
         dL = (2.0 * s / c.T).contiguous()
         ams, g = _timed(lambda: P.pmcmc_adjoint(tgt, opt, c.T, s0, s, acc, xid, ud, dL),
                         args.steps, 1, flush, stream, torch)
         budget = 256 * 1024 * 1024
         bms, gb = _timed(lambda: P.pmcmc_adjoint(tgt, opt, c.T, s0, s, acc, xid, ud, dL, budget),
                          1, 0, flush, stream, torch)
-        line.update(config=c.name, forward={"ms": fwd_ms, "newton_iters": res["iters"],
-                                            "status": res["status"], "accept_rate": res["accept_rate"],
+        line.update(config=c.name, forward={"ms": fwd_ms, "how": "sequential GPU loop",
+                                            "fixed_point_max_residual": fp_res,
+                                            "accept_rate": res["accept_rate"],
                                             "value": c.T / (fwd_ms / 1e3)},
                     adjoint={"ms": ams, "grad": g, "accepted": int(acc.sum().item())},
                     adjoint_recompute={"ms": bms, "grad": gb, "jac_budget_bytes": budget},
