@@ -87,6 +87,9 @@ def parse():
                     help="scan_sweep: comma list of T (overrides --scan-log2)")
     ap.add_argument("--scan-precisions", default="f32,f32_scan_bf16",
                     help="scan_sweep: precisions")
+    ap.add_argument("--c5-seq-after", type=int, default=150,
+                    help="c5: Newton sweeps after which an unconverged chain is completed by the "
+                         "sequential loop (0: Newton only)")
     ap.add_argument("--scan-kernel", choices=["rows", "staged"], default=None,
                     help="diagonal scan kernel for D <= 32 (default: the library's choice)")
     return ap.parse_args()
@@ -536,10 +539,12 @@ def run_other(args):
                                      torch.tensor(xi, device=dev), torch.tensor(u, device=dev),
                                      torch.empty((ch.T, ch.D), dtype=torch.float32, device=dev)))
             total += ch.T
-        opt = P.Options(jac="diag", precision="f32_scan_bf16", atol=1e-5, rtol=1e-5, clip=1)
+        opt = P.Options(jac="diag", precision="f32_scan_bf16", atol=1e-5, rtol=1e-5, clip=1,
+                        seq_after=args.c5_seq_after)
         ms, res = _timed(lambda: P.pmcmc_solve_batched(descs, opt), args.steps, args.warmup,
                          flush, stream, torch)
         iters = [r["iters"] for r in res]
+        n_seq = sum(r["sequential"] for r in res)
         # sequential GPU loop: the chains one after another would take sum of their times; run
         # each chain's sequential kernel on its own stream so they overlap on the device
         streams = [torch.cuda.Stream() for _ in range(16)]
@@ -561,6 +566,7 @@ def run_other(args):
                            "T~U[1024,65536]), bfloat16 pairs, eigenbasis of P or X^T X per chain",
                     value=total / (ms / 1e3), ms_per_step=ms,
                     samples=total, newton_iters={"max": max(iters), "mean": statistics.mean(iters)},
+                    seq_after=args.c5_seq_after, chains_completed_sequentially=n_seq,
                     converged=sum(r["status"] == "OK" for r in res), dtype="f32",
                     seq_gpu={"value": total / (sms / 1e3), "ms": sms, "speedup": sms / ms,
                              "how": "one sequential kernel per chain on 16 streams"})

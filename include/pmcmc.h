@@ -112,6 +112,8 @@ typedef struct {
     int spin_limit;       /* look-back wait bound (polls); 0 = default */
     int engine;           /* 0: automatic (tensor cores where a kernel exists: MALA on LOGREG,
                              F32, D <= 32, DIAG with gate_grad 0 or ZERO); 1: CUDA cores only */
+    int seq_after;        /* pmcmc_solve_batched: 0 = off; > 0 = a chain not converged after
+                             this many Newton sweeps is completed by the sequential loop */
 } pmcmc_options;
 
 typedef struct {
@@ -122,6 +124,8 @@ typedef struct {
     double min_margin;    /* min_t |log alpha_t - log u_t| of the returned iterate */
     int nonfinite_resets; /* elements of an iterate that were non-finite and were reset */
     float elapsed_ms;     /* device time of the solve (CUDA events) */
+    int sequential;       /* pmcmc_solve_batched with seq_after: 1 if the chain was completed by
+                             the sequential loop (its s_out is then the exact sequential chain) */
 } pmcmc_result;
 
 /* Fill `opt` with defaults: MALA, step 0.01, DIAG, F32, atol 1e-5, rtol 0, max_iters T,
@@ -256,6 +260,11 @@ typedef struct {
  * device-side loop runs until every chain has converged.  Uses opt->jac (DIAG or
  * DIAG_HUTCH), opt->precision (F32 or F32_SCAN_BF16), atol/rtol, max_iters, damping, clip.
  * Per-chain results go to res (B host structs, may be NULL).
+ * With opt->seq_after > 0 the Newton sweeps stop after seq_after sweeps (or max_iters, if
+ * smaller), and every chain not converged by then is recomputed by the sequential loop, several
+ * chains at once on separate streams; res[i].sequential marks those chains.  A chain whose
+ * Newton frontier advances a few steps per sweep costs less sequentially (Section 5.2 finds the
+ * same trade-off for batches).
  */
 pmcmc_status pmcmc_solve_batched(pmcmc_ctx *ctx, int B, const pmcmc_chain_desc *chains,
                                  const pmcmc_options *opt, pmcmc_result *res, void *stream);

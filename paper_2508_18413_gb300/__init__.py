@@ -118,6 +118,7 @@ class Options:
     chain_id: int = 0
     spin_limit: int = 0
     engine: str = "auto"   # "auto": tensor cores where a kernel exists; "simt": CUDA cores only
+    seq_after: int = 0     # batched: complete chains unconverged after this many sweeps sequentially
 
     def c(self) -> L.pmcmc_options:
         return L.pmcmc_options(SAMPLERS[self.sampler], float(self.step), int(self.leapfrog_L),
@@ -125,14 +126,14 @@ class Options:
                                float(self.rtol), int(self.max_iters), float(self.damping),
                                int(self.clip), int(self.gate_grad), int(self.seed),
                                int(self.chain_id), int(self.spin_limit),
-                               ENGINES[self.engine])
+                               ENGINES[self.engine], int(self.seq_after))
 
 
 def _result_dict(r: L.pmcmc_result) -> dict:
     return {"iters": r.iters, "status": STATUS_NAMES.get(r.status, r.status),
             "max_residual": r.max_residual, "accept_rate": r.accept_rate,
             "min_margin": r.min_margin, "nonfinite_resets": r.nonfinite_resets,
-            "elapsed_ms": r.elapsed_ms}
+            "elapsed_ms": r.elapsed_ms, "sequential": r.sequential}
 
 
 def pmcmc_gen_noise(seed: int, chain_id: int, T: int, D: int, precision: str = "f32",

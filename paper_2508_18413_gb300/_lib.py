@@ -32,13 +32,13 @@ class pmcmc_options(C.Structure):
                 ("rtol", C.c_double), ("max_iters", C.c_int), ("damping", C.c_double),
                 ("clip", C.c_int), ("gate_grad", C.c_int), ("seed", C.c_ulonglong),
                 ("chain_id", C.c_uint), ("spin_limit", C.c_int),
-                ("engine", C.c_int)]
+                ("engine", C.c_int), ("seq_after", C.c_int)]
 
 
 class pmcmc_result(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("max_residual", C.c_double),
                 ("accept_rate", C.c_double), ("min_margin", C.c_double),
-                ("nonfinite_resets", C.c_int), ("elapsed_ms", C.c_float)]
+                ("nonfinite_resets", C.c_int), ("elapsed_ms", C.c_float), ("sequential", C.c_int)]
 
 
 class pmcmc_chain_desc(C.Structure):

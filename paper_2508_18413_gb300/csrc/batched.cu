@@ -888,6 +888,61 @@ BatchTune batch_tune_lookup(pmcmc_ctx *c, int B, const pmcmc_chain_desc *chains,
                             const pmcmc_options *o, cudaStream_t st);
 }
 
+namespace pm {
+
+// Chains still unconverged after the Newton sweeps are recomputed by the sequential loop, up to
+// sixteen at once on the context's side streams (ordered after `st`, and `st` after them).
+static cudaError_t complete_sequential(pmcmc_ctx *c, int B, const pmcmc_chain_desc *ch,
+                                       pmcmc_result *rv, cudaStream_t st) {
+    std::vector<int> todo;
+    for (int i = 0; i < B; i++)
+        if (rv[i].status == PMCMC_NOT_CONVERGED) todo.push_back(i);
+    if (todo.empty()) return cudaSuccess;
+    for (cudaStream_t &q : c->seq_streams)
+        if (!q) {
+            cudaError_t e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+        }
+    for (cudaEvent_t &ev : c->seq_events)
+        if (!ev) {
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+    const int nq = std::min<int>(16, (int)todo.size());
+    cudaError_t e = cudaEventRecord(c->seq_events[16], st);
+    for (int k = 0; k < nq && e == cudaSuccess; k++) e = cudaStreamWaitEvent(c->seq_streams[k], c->seq_events[16], 0);
+    if (e != cudaSuccess) return e;
+    for (size_t j = 0; j < todo.size(); j++) {
+        const int i = todo[j];
+        const pmcmc_chain_desc &d = ch[i];
+        pmcmc_options so;
+        pmcmc_options_default(&so);
+        so.sampler = d.sampler;
+        so.step = d.step;
+        so.leapfrog_L = d.leapfrog_L;
+        so.precision = PMCMC_F32;
+        EvalArgs A;
+        fill_eval_args(A, &d.target, &so, d.T);
+        A.s0 = d.s0;
+        A.xi = d.xi;
+        A.u = d.u;
+        A.f_out = d.s_out;
+        cudaStream_t q = c->seq_streams[j % nq];
+        e = d.target.kind == PMCMC_LOGREG ? launch_seq_logreg(A, q) : launch_seq_small(A, q);
+        if (e != cudaSuccess) return e;
+        rv[i].status = PMCMC_OK;
+        rv[i].sequential = 1;
+        rv[i].max_residual = 0.0;
+    }
+    for (int k = 0; k < nq && e == cudaSuccess; k++) {
+        e = cudaEventRecord(c->seq_events[k], c->seq_streams[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->seq_events[k], 0);
+    }
+    return e;
+}
+
+}  // namespace pm
+
 extern "C" pmcmc_status pmcmc_solve_batched(pmcmc_ctx *c, int B, const pmcmc_chain_desc *chains,
                                             const pmcmc_options *o, pmcmc_result *res,
                                             void *stream) {
@@ -965,7 +1020,18 @@ extern "C" pmcmc_status pmcmc_solve_batched(pmcmc_ctx *c, int B, const pmcmc_cha
         use = rc.data();
     }
     BatchTune tune = batch_tune_lookup(c, B, use, o, st);
-    pmcmc_status ps = run_batched(c, B, use, o, res, st, tune, nullptr, true);
+    pmcmc_options ob = *o;
+    if (o->seq_after > 0 && (o->max_iters <= 0 || o->seq_after < o->max_iters)) ob.max_iters = o->seq_after;
+    std::vector<pmcmc_result> rv(B);
+    pmcmc_status ps = run_batched(c, B, use, &ob, rv.data(), st, tune, nullptr, true);
+    for (int i = 0; i < B; i++) rv[i].sequential = 0;
+    if (o->seq_after > 0 && ps >= 0) {
+        PM_CUDA_B(complete_sequential(c, B, use, rv.data(), st));
+        ps = PMCMC_OK;
+        for (int i = 0; i < B; i++)
+            if (rv[i].status != PMCMC_OK) ps = (pmcmc_status)rv[i].status;
+    }
+    if (res) std::copy(rv.begin(), rv.end(), res);
     if (any_q && ps >= 0) {
         for (int i = 0; i < B; i++)
             if (chains[i].target.Q)

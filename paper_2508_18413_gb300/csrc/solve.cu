@@ -164,6 +164,7 @@ void pmcmc_options_default(pmcmc_options *o) {
     o->chain_id = 0;
     o->spin_limit = 0;
     o->engine = 0;
+    o->seq_after = 0;
 }
 
 pmcmc_status pmcmc_create(pmcmc_ctx **out, int device) {
@@ -206,6 +207,10 @@ pmcmc_status pmcmc_destroy(pmcmc_ctx *c) {
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->batch_graph_exec) cudaGraphExecDestroy(c->batch_graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaStream_t &q : c->seq_streams)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t &e : c->seq_events)
+        if (e) cudaEventDestroy(e);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->ws) cudaFree(c->ws);
     if (c->aux) cudaFree(c->aux);

@@ -50,6 +50,8 @@ struct pmcmc_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::string graph_key;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t seq_streams[16] = {};  // batched: concurrent sequential completions
+    cudaEvent_t seq_events[17] = {};
     int no_graph = 0;
     unsigned long long flags_generation = ~0ull;
     size_t flags_offset = 0, flags_zeroed = 0;

@@ -125,3 +125,21 @@ def test_batched_with_basis_matches_oracle():
     for (_, ref, margin), d, r in zip(chains, descs, res):
         assert r["status"] == "OK", (d.sampler, d.target.kind, d.target.D, r)
         _check(d, ref, margin)
+
+
+def test_batched_sequential_completion_matches_oracle():
+    """With seq_after, chains not converged after that many Newton sweeps are recomputed by the
+    sequential loop; every chain must then equal the oracle trace."""
+    chains = _chains(SPEC, seed=5)
+    descs = [c[0] for c in chains]
+    opt = P.Options(jac="diag", precision="f32", atol=1e-6, rtol=1e-6, clip=1)
+    full = P.pmcmc_solve_batched(descs, opt)
+    cap = int(np.median([r["iters"] for r in full]))   # about half the chains need more sweeps
+    opt.seq_after = cap
+    res = P.pmcmc_solve_batched(descs, opt)
+    assert any(r["sequential"] for r in res) and not all(r["sequential"] for r in res)
+    for (desc, ref, margin), r, rf in zip(chains, res, full):
+        assert r["status"] == "OK", (desc.sampler, desc.target.kind, desc.target.D, r)
+        assert r["iters"] <= cap
+        assert r["sequential"] == (rf["iters"] > cap)
+        _check(desc, ref, margin)
