@@ -90,7 +90,7 @@ def parse():
     ap.add_argument("--c5-seq-after", type=int, default=150,
                     help="c5: Newton sweeps after which an unconverged chain is completed by the "
                          "sequential loop (0: Newton only)")
-    ap.add_argument("--scan-kernel", choices=["rows", "staged"], default=None,
+    ap.add_argument("--scan-kernel", choices=["rows", "staged", "pipe"], default=None,
                     help="diagonal scan kernel for D <= 32 (default: the library's choice)")
     return ap.parse_args()
 
@@ -579,14 +579,14 @@ def run_other(args):
                   [(1 << int(k)) // D for k in args.scan_log2.split(",")])
             for T in Ts:
                 n = T * D
-                sd = torch.float32
+                sd = torch.float64 if prec == "f64" else torch.float32
                 ad = torch.bfloat16 if prec == "f32_scan_bf16" else sd
                 a = (torch.rand((T, D), device=dev) * 1.8 - 0.9).to(ad)
                 b = torch.randn((T, D), device=dev).to(ad)
                 sv = torch.randn((T, D), device=dev, dtype=sd)
                 ms, _ = _timed(lambda: P.pmcmc_scan("diag", prec, a, b, sv), args.steps, args.warmup,
                                flush, stream, torch)
-                bytes_ = n * (a.element_size() * 2 + 8)
+                bytes_ = n * (a.element_size() + sv.element_size()) * 2
                 gbs = bytes_ / (ms / 1e3) / 1e9
                 rows.append({"precision": prec, "elements": n, "T": T, "D": D, "ms": ms,
                              "GB/s": gbs, "frac_of_measured_hbm": gbs / peak})

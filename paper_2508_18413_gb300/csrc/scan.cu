@@ -11,6 +11,8 @@
 //
 // A non-finite updated element is reset (to s_reset, or 0): the fixed point is finite, and an
 // iterate poisoned by an overflow would otherwise stop the Newton iteration from progressing.
+#include <algorithm>
+#include <numeric>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -801,7 +803,210 @@ scan_diag_staged_kernel(int T, int D, int TT, const S *__restrict__ a, const S *
     finish_tile(ctl, ntiles);
 }
 
+// ==========================================================================================
+// Diagonal scan, D <= 32, persistent and double-buffered: one CTA per SM holds two shared-memory
+// tile buffers.  While the CTA scans tile k from one buffer, the bulk copies of the next tile it
+// took a ticket for are already filling the other, so every SM keeps a tile's worth of reads in
+// flight through its own look-back and compute.  Each element of a, b and s is read from HBM
+// once, by a bulk copy (the sub-16-byte tail of a ragged last tile by plain loads).
+//
+// Within a tile each of the P = 32 / D lane groups of a warp (lane = q D + d) owns a contiguous
+// run of M timesteps of channel d, which it composes (pass 1) and later applies (pass 2) one
+// timestep at a time in registers; only the P group aggregates of a warp are combined across
+// lanes.  The run length satisfies (M - 1) D = 0 mod 64 where the tile size allows, so the P
+// groups' shared-memory words fall in distinct banks.
+//
+// Ordering.  Tickets are taken in increasing order and each CTA processes its tickets in the
+// order taken, so the lowest tile without a published aggregate is always the current tile of
+// a running CTA that is not waiting: the look-back cannot deadlock on a prefetched tile.
+// ==========================================================================================
+template <typename R, typename S>
+__global__ void __launch_bounds__(256, 1)
+scan_diag_pipe_kernel(int T, int D, int M, const S *__restrict__ a, const S *__restrict__ b,
+                      R *__restrict__ s, const R *__restrict__ s_reset, unsigned int *flags,
+                      R *__restrict__ gagg, R *__restrict__ gincl, ScanCtl *ctl, EvalStats *stats,
+                      const int *skip, unsigned int spin_limit) {
+    if (skip && *(volatile const int *)skip) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long s_mbar[2];
+    __shared__ unsigned int s_first, s_next[2], s_epoch;
+    __shared__ R wA[8][32], wB[8][32];
+    __shared__ R cin[8][32];
+    __shared__ R tA[32], tB[32], ccar[32];
+    const int P = 32 / D, L = P * D;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int TT = 8 * P * M;  // timesteps per tile
+    const unsigned int ntiles = (unsigned int)ceil_div(T, TT);
+    const size_t E = (size_t)TT * D;
+    const size_t ab_region = (E * sizeof(S) + 15) & ~(size_t)15;
+    const size_t s_region = (E * sizeof(R) + 15) & ~(size_t)15;
+    const size_t buf_bytes = 2 * ab_region + s_region;
+    const uint32_t mbar0 = tc::smem_u32(&s_mbar[0]);
 
+    // start the bulk copies of `tile` into buffer `bi` (one thread)
+    auto issue = [&](unsigned int tile, int bi) {
+        const long long t0 = (long long)tile * TT;
+        const int Ev = (int)min((long long)TT, (long long)T - t0) * D;
+        const size_t base = (size_t)t0 * D;
+        unsigned char *buf = smem_raw + (size_t)bi * buf_bytes;
+        const uint32_t ab_bytes = (uint32_t)(((size_t)Ev * sizeof(S)) & ~(size_t)15);
+        const uint32_t s_bytes = (uint32_t)(((size_t)Ev * sizeof(R)) & ~(size_t)15);
+        const uint32_t bar = mbar0 + 8u * (uint32_t)bi;
+        tc::mbar_arrive_expect_tx(bar, 2 * ab_bytes + s_bytes);
+        if (ab_bytes) {
+            tc::bulk_g2s(tc::smem_u32(buf), a + base, ab_bytes, bar);
+            tc::bulk_g2s(tc::smem_u32(buf + ab_region), b + base, ab_bytes, bar);
+        }
+        if (s_bytes) tc::bulk_g2s(tc::smem_u32(buf + 2 * ab_region), s + base, s_bytes, bar);
+    };
+
+    if (threadIdx.x == 0) {
+        tc::mbar_init(mbar0, 1);
+        tc::mbar_init(mbar0 + 8u, 1);
+        tc::fence_barrier_init();
+        const unsigned int t = atomicAdd(&ctl->ticket, 1u);
+        s_first = t;
+        s_epoch = *(volatile unsigned int *)&ctl->epoch;
+        if (t < ntiles) issue(t, 0);
+    }
+    __syncthreads();
+    const unsigned int epoch = s_epoch;
+    const bool lane_on = lane < L;
+    const int d = lane_on ? lane % D : 0;
+    const int q = lane_on ? lane / D : 0;
+    const int last_lane = (P - 1) * D + d;  // lane holding the warp aggregate of channel d
+    const int tg = (w * P + q) * M;         // first local timestep of this lane group's run
+    R dmax = R(0);
+    unsigned int resets = 0;
+    unsigned int cur = s_first;
+    for (int it = 0; cur < ntiles; it++) {
+        const int bi = it & 1;
+        const int tile = (int)cur;
+        // the other buffer was released by the barrier that ended the previous iteration
+        if (threadIdx.x == 0) {
+            const unsigned int nx = atomicAdd(&ctl->ticket, 1u);
+            s_next[bi] = nx;
+            if (nx < ntiles) {
+                tc::fence_async_smem();  // earlier generic writes to that buffer (tail loads)
+                issue(nx, bi ^ 1);
+            }
+        }
+        const long long t0 = (long long)tile * TT;
+        const int TTv = (int)min((long long)TT, (long long)T - t0);
+        const int Ev = TTv * D;
+        const size_t base = (size_t)t0 * D;
+        unsigned char *buf = smem_raw + (size_t)bi * buf_bytes;
+        S *sa = reinterpret_cast<S *>(buf);
+        S *sbv = reinterpret_cast<S *>(buf + ab_region);
+        R *ss = reinterpret_cast<R *>(buf + 2 * ab_region);
+        // the copies complete on their own; the bound only guards against a lost completion
+        if (!tc::mbar_wait_drain(mbar0 + 8u * (uint32_t)bi, (uint32_t)(it >> 1) & 1u, 1u << 20) &&
+            threadIdx.x == 0)
+            atomicExch(&ctl->timeout, 1u);
+        const int ab_done = (int)((((size_t)Ev * sizeof(S)) & ~(size_t)15) / sizeof(S));
+        const int s_done = (int)((((size_t)Ev * sizeof(R)) & ~(size_t)15) / sizeof(R));
+        if (ab_done < Ev || s_done < Ev) {  // uniform: only a ragged last tile
+            for (int e = ab_done + threadIdx.x; e < Ev; e += 256) {
+                sa[e] = a[base + e];
+                sbv[e] = b[base + e];
+            }
+            for (int e = s_done + threadIdx.x; e < Ev; e += 256) ss[e] = s[base + e];
+            __syncthreads();
+        }
+        const int mv = lane_on ? max(0, min(M, TTv - tg)) : 0;  // timesteps of the run in range
+
+        // pass 1: the run's composed map, one timestep at a time
+        R GA = R(1), GB = R(0);
+#pragma unroll 4
+        for (int j = 0; j < mv; j++) {
+            const int e = (tg + j) * D + d;
+            const R ra = load_as<S, R>(sa + e);
+            GB = ra * GB + load_as<S, R>(sbv + e);
+            GA = ra * GA;
+        }
+        // inclusive scan over the P runs of the warp (channel-segmented, later run on the left)
+        R IA = GA, IB = GB;
+        for (int off = D; off < L; off <<= 1) {
+            const R pa = __shfl_up_sync(0xffffffffu, IA, off);
+            const R pb = __shfl_up_sync(0xffffffffu, IB, off);
+            if (lane_on && lane >= off) {
+                IB = IA * pb + IB;
+                IA = IA * pa;
+            }
+        }
+        {
+            const R ea = __shfl_sync(0xffffffffu, IA, last_lane);
+            const R eb = __shfl_sync(0xffffffffu, IB, last_lane);
+            if (lane < D) {
+                wA[w][lane] = ea;
+                wB[w][lane] = eb;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < D) {
+            const int dd = threadIdx.x;
+            R TA_ = R(1), TB_ = R(0);
+            for (int k = 0; k < 8; k++) {
+                TB_ = wA[k][dd] * TB_ + wB[k][dd];
+                TA_ = wA[k][dd] * TA_;
+            }
+            tA[dd] = TA_;
+            tB[dd] = TB_;
+            if (tile == 0) {
+                gincl[dd] = TB_;
+            } else {
+                gagg[((size_t)tile * 2) * D + dd] = TA_;
+                gagg[((size_t)tile * 2 + 1) * D + dd] = TB_;
+            }
+            ccar[dd] = R(0);
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
+        if (tile > 0) {
+            lookback_block64<R>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, ccar);
+            if (threadIdx.x < D) {
+                gincl[(size_t)tile * D + threadIdx.x] = tA[threadIdx.x] * ccar[threadIdx.x] + tB[threadIdx.x];
+                __threadfence();
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) st_release(flags + tile, make_flag(epoch, kFlagIncl));
+        }
+        if (threadIdx.x < D) {
+            const int dd = threadIdx.x;
+            R pa = R(1), pb = R(0);
+            const R c = ccar[dd];
+            for (int k = 0; k < 8; k++) {
+                cin[k][dd] = pa * c + pb;
+                pb = wA[k][dd] * pb + wB[k][dd];
+                pa = wA[k][dd] * pa;
+            }
+        }
+        __syncthreads();
+        // pass 2: the carry into the run (the end of the previous run of the warp), then the
+        // run's timesteps in order; s streamed out
+        const R cw = lane_on ? cin[w][d] : R(0);
+        R delta = __shfl_up_sync(0xffffffffu, IA * cw + IB, D);
+        if (lane < D) delta = cw;
+#pragma unroll 4
+        for (int j = 0; j < mv; j++) {
+            const int e = (tg + j) * D + d;
+            delta = load_as<S, R>(sa + e) * delta + load_as<S, R>(sbv + e);
+            R sn = ss[e] + delta;
+            if (!finite(sn)) {
+                sn = s_reset ? s_reset[d] : R(0);
+                resets++;
+            } else {
+                dmax = max(dmax, fabs(delta));
+            }
+            __stcs(s + base + e, sn);
+        }
+        __syncthreads();  // this buffer is free for the copy issued next iteration
+        cur = s_next[bi];
+    }
+    if (stats) block_stats(stats, (double)dmax, resets);
+    exit_persistent(ctl);
+}
 
 // Timesteps per tile of the staged kernel: about 8K elements (4K in FP64), a multiple of the
 // 8 P timesteps of a CTA's rows (P = 32 / D), and small enough to give every SM two tiles.
@@ -818,19 +1023,39 @@ static size_t staged_smem(int TT, int D, int rbytes, int sbytes) {
     return 2 * ((E * sbytes + 15) & ~(size_t)15) + E * rbytes;
 }
 
-// The register-resident kernel is the default (measured faster on GB300 at 2^20..2^28
-// elements); PMCMC_SCAN_KERNEL=staged selects the bulk-copy staged kernel (measurements).
-static bool staged_enabled() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("PMCMC_SCAN_KERNEL");
-        v = (e && strcmp(e, "staged") == 0) ? 1 : 0;
-    }
-    return v == 1;
+// Run length M of the pipelined kernel (its tile is 8 P M timesteps): two tile buffers of a, b
+// and s within about 216 KB of shared memory, at least two tiles per SM where T allows, and
+// M - 1 a multiple of 32 / gcd(D, 32) (the P runs of a warp then start in distinct banks) unless
+// that would halve the run.
+static int pipe_run(int T, int D, int sbytes, int rbytes) {
+    const int P = 32 / D;
+    const int per_elem = 2 * sbytes + rbytes;
+    const int m_max = std::max(1, (108 * 1024) / (8 * P * D * per_elem));
+    const int spread = std::max(1, ceil_div(T, 2 * 152 * 8 * P));
+    const int cap = std::min(m_max, spread);
+    if (P == 1) return cap;
+    const int c = 32 / std::gcd(D, 32);
+    const int m = (cap - 1) / c * c + 1;
+    return 2 * m >= cap ? m : cap;
+}
+
+static size_t pipe_smem(int M, int D, int sbytes, int rbytes) {
+    const size_t E = (size_t)8 * (32 / D) * M * D;
+    return 2 * (2 * ((E * sbytes + 15) & ~(size_t)15) + ((E * rbytes + 15) & ~(size_t)15));
+}
+
+// Kernel choice for D <= 32: the register-resident kernels by default; PMCMC_SCAN_KERNEL=staged
+// or =pipe selects the bulk-copy staged or the pipelined kernel (read at every launch, so a
+// process can compare them).
+static int scan_kernel_choice() {
+    const char *e = getenv("PMCMC_SCAN_KERNEL");
+    return !e ? 0 : strcmp(e, "staged") == 0 ? 1 : strcmp(e, "pipe") == 0 ? 2 : 0;
 }
 
 int diag_scan_tile(int T, int D, int elem_bytes) {
-    if (D <= 32) return std::min(diag_scan_tile_rows(T, D), staged_tile(T, D, elem_bytes));
+    if (D <= 32)  // the smallest tile of the kernels that may run sizes the workspace
+        return std::min({diag_scan_tile_rows(T, D), staged_tile(T, D, elem_bytes),
+                         8 * (32 / D) * pipe_run(T, D, elem_bytes, elem_bytes)});
     // enough tiles to fill the GPU twice over, at most ~4096 elements (FP32) per tile
     const int max_elems = elem_bytes >= 8 ? 2048 : 4096;
     int tt_max = std::max(8, (max_elems / std::max(D, 1)) / 8 * 8);
@@ -905,24 +1130,27 @@ static void diag_shape(int T, int D, int *rows, int *nsub) {
     }
 }
 
-// CTAs of `kernel` (block of `threads`, no dynamic shared memory) resident on the device at
-// once, cached per kernel.
+// CTAs of `kernel` (block of `threads`, `dyn_smem` bytes of dynamic shared memory) resident on
+// the device at once, cached per kernel and shared-memory size.
 template <class K>
-static int resident_ctas(K kernel, int threads) {
-    static const void *keys[16] = {};
-    static int vals[16] = {};
+static int resident_ctas(K kernel, int threads, size_t dyn_smem = 0) {
+    static const void *keys[32] = {};
+    static size_t smems[32] = {};
+    static int vals[32] = {};
     static int n = 0;
     const void *key = reinterpret_cast<const void *>(kernel);
     for (int i = 0; i < n; i++)
-        if (keys[i] == key) return vals[i];
+        if (keys[i] == key && smems[i] == dyn_smem) return vals[i];
     int per_sm = 1, dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn_smem) != cudaSuccess ||
+        per_sm < 1)
         per_sm = 1;
     const int v = per_sm * sms;
-    if (n < 16) {
+    if (n < 32) {
         keys[n] = key;
+        smems[n] = dyn_smem;
         vals[n++] = v;
     }
     return v;
@@ -990,13 +1218,37 @@ static cudaError_t run_scan_staged(int T, int D, const void *a, const void *b, v
     return cudaGetLastError();
 }
 
+template <typename R, typename S>
+static cudaError_t run_scan_pipe(int T, int D, const void *a, const void *b, void *s,
+                                 const void *s_reset, const ScanWork &w, EvalStats *stats,
+                                 const int *skip, unsigned int spin, cudaStream_t st) {
+    const int M = pipe_run(T, D, sizeof(S), sizeof(R));
+    const int ntiles = ceil_div(T, 8 * (32 / D) * M);
+    if (ntiles > w.max_tiles) return cudaErrorInvalidValue;
+    const size_t sm = pipe_smem(M, D, sizeof(S), sizeof(R));
+    auto k = scan_diag_pipe_kernel<R, S>;
+    cudaError_t e = ensure_dyn_smem(k, sm);
+    if (e != cudaSuccess) return e;
+    // persistent: every CTA must be resident at once (the look-back waits on other CTAs)
+    k<<<std::min(ntiles, resident_ctas(k, 256, sm)), 256, sm, st>>>(
+        T, D, M, (const S *)a, (const S *)b, (R *)s, (const R *)s_reset, w.flags, (R *)w.agg,
+        (R *)w.incl, w.ctl, stats, skip, spin);
+    return cudaGetLastError();
+}
+
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, const void *a,
                              const void *b, void *s, const void *s_reset, const ScanWork &w,
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st) {
-    if (D <= 32 && staged_enabled() && aligned16(a) && aligned16(b) && aligned16(s)) {
+    if (D <= 32 && scan_kernel_choice() == 2 && aligned16(a) && aligned16(b) && aligned16(s)) {
+        if (f64) return run_scan_pipe<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+        if (storage == 1)
+            return run_scan_pipe<float, __nv_bfloat16>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+        return run_scan_pipe<float, float>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
+    }
+    if (D <= 32 && scan_kernel_choice() == 1 && aligned16(a) && aligned16(b) && aligned16(s)) {
         if (f64) return run_scan_staged<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
         if (storage == 1)
             return run_scan_staged<float, __nv_bfloat16>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
