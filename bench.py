@@ -511,12 +511,19 @@ def run_other(args):
         budget = 256 * 1024 * 1024
         bms, gb = _timed(lambda: P.pmcmc_adjoint(tgt, opt, c.T, s0, s, acc, xid, ud, dL, budget),
                          1, 0, flush, stream, torch)
+        # the same adjoint with the J's formed on the CUDA cores (comparison)
+        sopt2 = P.Options(sampler="mala", step=c.step, jac="diag", precision="f32", atol=c.tol,
+                          clip=1, gate_grad=0, engine="simt")
+        cms, gc = _timed(lambda: P.pmcmc_adjoint(tgt, sopt2, c.T, s0, s, acc, xid, ud, dL),
+                         1, 0, flush, stream, torch)
         line.update(config=c.name, forward={"ms": fwd_ms, "how": "sequential GPU loop",
                                             "fixed_point_max_residual": fp_res,
                                             "accept_rate": res["accept_rate"],
                                             "value": c.T / (fwd_ms / 1e3)},
                     adjoint={"ms": ams, "grad": g, "accepted": int(acc.sum().item())},
                     adjoint_recompute={"ms": bms, "grad": gb, "jac_budget_bytes": budget},
+                    adjoint_cuda_cores={"ms": cms, "grad": gc,
+                                        "how": "J formed by the CUDA-core kernel (engine simt)"},
                     value=c.T / ((fwd_ms + ams) / 1e3), ms_per_step=fwd_ms + ams, dtype="f32")
     elif wl == "c5":
         chains = W.batched_mix(512)

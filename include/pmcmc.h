@@ -111,7 +111,8 @@ typedef struct {
     unsigned int chain_id;   /* noise counter of this chain */
     int spin_limit;       /* look-back wait bound (polls); 0 = default */
     int engine;           /* 0: automatic (tensor cores where a kernel exists: MALA on LOGREG,
-                             F32, D <= 32, DIAG with gate_grad 0 or ZERO); 1: CUDA cores only */
+                             F32, D <= 32, DIAG with gate_grad 0 or ZERO; the adjoint's dense
+                             Jacobians on LOGREG, F32, 64 < D <= 128); 1: CUDA cores only */
     int seq_after;        /* pmcmc_solve_batched: 0 = off; > 0 = a chain not converged after
                              this many Newton sweeps is completed by the sequential loop */
 } pmcmc_options;
@@ -212,7 +213,10 @@ pmcmc_status pmcmc_scan(pmcmc_ctx *ctx, pmcmc_jac kind, pmcmc_precision precisio
  * as a parallel reverse scan with dense J_{t+1} = I + step H(s_t) (accepted) or I (rejected),
  * and returns dL/dtheta = sum_t lambda_t^T d f_t/d theta for theta = (step, prior_scale).
  * J is recomputed in segments when T*D*D reals exceed jac_budget_bytes (0 = no limit).
- * PMCMC_MALA with LOGREG (D <= 128 in FP32, 64 in FP64) or GAUSSIAN targets.
+ * PMCMC_MALA with LOGREG (D <= 128 in FP32, 64 in FP64) or GAUSSIAN targets.  With LOGREG in
+ * FP32 and 64 < D <= 128 the J's are formed on the tensor cores (split-tf32 products of FP32
+ * accuracy; opt->engine = 1 selects the CUDA-core kernel).  The workspace then also holds an
+ * image of X^T of 32 KiB per 32 data rows.
  * s: the converged trajectory; acc: its T decisions (device bytes); u is not used (the
  * decisions are given).  lambda_out (T x D device reals, may be NULL) receives lambda.
  * grad_out: 2 host doubles, dL/dstep and dL/dprior_scale (zero for Gaussian targets).

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "hess_tc.h"
 #include "solve.h"
 
 namespace pm {
@@ -549,6 +550,9 @@ extern "C" pmcmc_status pmcmc_adjoint(pmcmc_ctx *c, const pmcmc_target *tg,
     const size_t o_agg = cv.take((size_t)rb * max_tiles * (DD + D));
     const size_t o_incl = cv.take((size_t)rb * max_tiles * D);
     const size_t o_theta = cv.take(2 * sizeof(double));
+    // 64 < D <= 128, FP32: the J's are formed on the tensor cores from an image of X^T
+    const bool hess_tc = !gauss && !f64 && o->engine != 1 && hess_tc_supported(D, tg->N);
+    const size_t o_img = hess_tc ? cv.take(hess_tc_image_bytes(tg->N)) : 0;
     pmcmc_status ps = ws_reserve(c, cv.used);
     if (ps != PMCMC_OK) return ps;
     char *base = (char *)c->ws;
@@ -576,6 +580,8 @@ extern "C" pmcmc_status pmcmc_adjoint(pmcmc_ctx *c, const pmcmc_target *tg,
             adj_hess_gauss_kernel<float><<<ceil_div(DD, 256), 256, 0, st>>>(D, (const float *)tg->prec, (float)eps, (float *)Jbuf);
         PM_CUDA_A(cudaGetLastError());
     }
+    if (hess_tc)
+        PM_CUDA_A(launch_hess_tc_pack((const float *)tg->X, tg->N, D, base + o_img, st));
     std::vector<int> jmap(max_seg);
     // the accepted list is sorted; locate each segment's range by binary search
     for (size_t si = 0; si < segs.size(); si++) {
@@ -589,7 +595,12 @@ extern "C" pmcmc_status pmcmc_adjoint(pmcmc_ctx *c, const pmcmc_target *tg,
         for (int i = 0; i < n; i++) jmap[i] = -1;
         for (int i = 0; i < cnt; i++) jmap[accepted[first + i] - t_lo - 1] = i;
         PM_CUDA_A(cudaMemcpyAsync(jmap_d, jmap.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-        if (!gauss && cnt > 0) {
+        if (hess_tc && cnt > 0) {
+            PM_CUDA_A(launch_hess_logreg_tc(cnt, list_d + first, D, tg->N, base + o_img,
+                                            (const float *)s0, (const float *)s, (float)eps,
+                                            (float)(1.0 / (sp * sp)), (float *)Jbuf,
+                                            &c->ctl->scan.timeout, spin, st));
+        } else if (!gauss && cnt > 0) {
             dim3 grid(ceil_div(cnt, 4), ceil_div(D, 64), ceil_div(D, 64));
             if (f64)
                 adj_hess_logreg_kernel<double><<<grid, 256, 0, st>>>(
@@ -635,7 +646,7 @@ extern "C" pmcmc_status pmcmc_adjoint(pmcmc_ctx *c, const pmcmc_target *tg,
     if (hc->scan.timeout) {
         unsigned int zero = 0;
         cudaMemcpy(&c->ctl->scan.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice);
-        return set_error(c, PMCMC_ETIMEOUT, "adjoint: a look-back wait ran out");
+        return set_error(c, PMCMC_ETIMEOUT, "adjoint: a bounded wait (look-back or Jacobian pipeline) ran out");
     }
     grad_out[0] = h[0];
     grad_out[1] = h[1];

@@ -1044,12 +1044,18 @@ static size_t pipe_smem(int M, int D, int sbytes, int rbytes) {
     return 2 * (2 * ((E * sbytes + 15) & ~(size_t)15) + ((E * rbytes + 15) & ~(size_t)15));
 }
 
-// Kernel choice for D <= 32: the register-resident kernels by default; PMCMC_SCAN_KERNEL=staged
-// or =pipe selects the bulk-copy staged or the pipelined kernel (read at every launch, so a
-// process can compare them).
-static int scan_kernel_choice() {
+// Kernel choice for D <= 32.  By default the pipelined kernel for 2^21 < T D <= 3 * 2^22
+// elements and the register-resident kernels otherwise (measured on GB300, D = 2, 8, 25: the
+// pipelined kernel runs 1.5-2x faster in that range, where the row kernel's tiles are either
+// small or few per SM, and slower above it, where its one tile in flight per SM leaves the
+// look-back latency exposed).  PMCMC_SCAN_KERNEL=rows, staged or pipe forces a kernel (read at
+// every launch, so a process can compare them).
+static int scan_kernel_choice(long long elems) {
     const char *e = getenv("PMCMC_SCAN_KERNEL");
-    return !e ? 0 : strcmp(e, "staged") == 0 ? 1 : strcmp(e, "pipe") == 0 ? 2 : 0;
+    if (e && strcmp(e, "rows") == 0) return 0;
+    if (e && strcmp(e, "staged") == 0) return 1;
+    if (e && strcmp(e, "pipe") == 0) return 2;
+    return (elems > (1ll << 21) && elems <= 3ll * (1ll << 22)) ? 2 : 0;
 }
 
 int diag_scan_tile(int T, int D, int elem_bytes) {
@@ -1242,13 +1248,14 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
                              const void *b, void *s, const void *s_reset, const ScanWork &w,
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st) {
-    if (D <= 32 && scan_kernel_choice() == 2 && aligned16(a) && aligned16(b) && aligned16(s)) {
+    const int choice = D <= 32 ? scan_kernel_choice((long long)T * D) : 0;
+    if (D <= 32 && choice == 2 && aligned16(a) && aligned16(b) && aligned16(s)) {
         if (f64) return run_scan_pipe<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
         if (storage == 1)
             return run_scan_pipe<float, __nv_bfloat16>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
         return run_scan_pipe<float, float>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
     }
-    if (D <= 32 && scan_kernel_choice() == 1 && aligned16(a) && aligned16(b) && aligned16(s)) {
+    if (D <= 32 && choice == 1 && aligned16(a) && aligned16(b) && aligned16(s)) {
         if (f64) return run_scan_staged<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
         if (storage == 1)
             return run_scan_staged<float, __nv_bfloat16>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);

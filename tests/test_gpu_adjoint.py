@@ -119,3 +119,58 @@ def test_autograd_function_matches_adjoint_and_finite_differences():
     fd_s = (L(0.02, 1.2 + h) - L(0.02, 1.2 - h)) / (2 * h)
     assert float(ge) == pytest.approx(fd_e, rel=1e-5)
     assert float(gs) == pytest.approx(fd_s, rel=1e-5)
+
+
+# ------------------------------------------------------------------------------------------
+# 64 < D <= 128 in FP32: the J's come from the tensor-core kernel (split-tf32 products)
+# ------------------------------------------------------------------------------------------
+
+def _wide_setup(T=500, D=100, N=700, eps=0.002):
+    # step 0.002 accepts ~90% of the steps at D = 100, N = 700; 22 data-row chunks of 32 (ragged)
+    return _setup("logreg", T=T, D=D, N=N, eps=eps, dt=torch.float32)
+
+
+@pytest.mark.parametrize("D,N", [(100, 700), (128, 97), (65, 300)])
+def test_adjoint_tensor_core_jacobians_match_oracle(D, N):
+    args, g_ref, _ = _wide_setup(D=D, N=N)
+    ge, gs = P.pmcmc_adjoint(*args)
+    assert ge == pytest.approx(g_ref[0], rel=1e-4)
+    assert gs == pytest.approx(g_ref[1], rel=1e-4)
+    # the CUDA-core kernel on the same inputs
+    gt, opt = args[0], args[1]
+    simt = P.Options(sampler="mala", step=opt.step, precision="f32", engine="simt")
+    ge2, gs2 = P.pmcmc_adjoint(gt, simt, *args[2:])
+    assert ge == pytest.approx(ge2, rel=2e-5)
+    assert gs == pytest.approx(gs2, rel=2e-5)
+
+
+def test_adjoint_tensor_core_lambda_satisfies_reverse_recursion():
+    """Every step's J from the tensor-core kernel, checked through lambda_t = dL/ds_t +
+    J_{t+1}^T lambda_{t+1} with the oracle's J (FP32 products: 1e-4 relative to the terms)."""
+    T, D = 300, 100
+    args, _, (p, s, acc, dLds) = _wide_setup(T=T, D=D)
+    _, _, lam = P.pmcmc_adjoint(*args, want_lambda=True)
+    lam = lam.double().cpu().numpy()
+    p0 = O.Problem(p.target, "mala", p.eps, xi=p.xi, u=p.u, gate_grad=0)
+    checked = 0
+    for t in range(T - 1):
+        if not acc[t + 1]:
+            continue
+        J = O.jacobian(p0, t + 2, s[t], "dense")
+        term = J.T @ lam[t + 1]
+        scale = np.abs(J.T) @ np.abs(lam[t + 1]) + np.abs(dLds[t])
+        assert np.all(np.abs(lam[t] - dLds[t] - term) <= 1e-4 * scale + 1e-9), t
+        checked += 1
+    assert checked > T // 2
+
+
+@pytest.mark.parametrize("budget_mats", [1, 7])
+def test_adjoint_tensor_core_segments_agree(budget_mats):
+    """Segments that rebuild a few J's each (single-step and odd pair counts) give the gradient
+    of the one-segment run."""
+    D = 100
+    args, g_ref, _ = _wide_setup(T=200, D=D, N=300)
+    full = P.pmcmc_adjoint(*args)
+    seg = P.pmcmc_adjoint(*args, jac_budget_bytes=budget_mats * D * D * 4)
+    np.testing.assert_allclose(seg, full, rtol=1e-5)
+    assert full[0] == pytest.approx(g_ref[0], rel=1e-4)
