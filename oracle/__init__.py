@@ -21,13 +21,13 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "Target", "Problem", "logp", "grad", "hess", "mala_step", "hmc_step", "leapfrog",
+    "Target", "Problem", "logp", "grad", "hess", "mala_step", "hmc_step", "leapfrog", "gibbs_sweep",
     "f", "chain", "jacobian", "deer", "mala_chain_frozen", "mala_adjoint", "philox4x32_10",
     "gen_noise", "SAMPLERS", "JACS",
 ]
 
-SAMPLERS = {"mala": 0, "hmc": 1, "leapfrog": 2, "ula": 3}
-TARGETS = {"gaussian": 0, "logreg": 1, "banana": 2}
+SAMPLERS = {"mala": 0, "hmc": 1, "leapfrog": 2, "ula": 3, "gibbs": 4}
+TARGETS = {"gaussian": 0, "logreg": 1, "banana": 2, "schools": 3}
 JACS = {"dense": 0, "diag": 1, "block2": 2, "zero": 4}
 
 _dp = C.POINTER(C.c_double)
@@ -74,7 +74,9 @@ def _ptr(a, typ=_dp):
 
 @dataclass
 class Target:
-    """A target density: 'gaussian' (mu, P = precision), 'logreg' (X, y, sigma_p), 'banana'."""
+    """A target density: 'gaussian' (mu, P = precision), 'logreg' (X, y, sigma_p), 'banana',
+    or 'schools' (the hierarchical Gaussian model of the Gibbs experiment, Appendix B.1: X holds
+    the scores, S schools x N students, and D = 2 + 2 S)."""
     kind: str
     D: int
     mu: np.ndarray | None = None
@@ -90,7 +92,11 @@ class Target:
         self.y = _arr(self.y)
         if self.kind == "banana":
             assert self.D == 2
-        self._c = _CTarget(TARGETS[self.kind], self.D, 0 if self.X is None else self.X.shape[0],
+        rows = 0 if self.X is None else self.X.shape[0]
+        if self.kind == "schools":
+            assert self.X.ndim == 2 and self.D == 2 + 2 * self.X.shape[0]
+            rows = self.X.shape[1]  # scores per school
+        self._c = _CTarget(TARGETS[self.kind], self.D, rows,
                            _ptr(self.mu), _ptr(self.P), _ptr(self.X), _ptr(self.y),
                            float(self.sigma_p))
 
@@ -171,6 +177,16 @@ def leapfrog(t: Target, eps, s):
     out = np.zeros(2 * t.D)
     _load().o_leapfrog(C.byref(t._c), C.c_double(eps), _ptr(s), _ptr(out))
     return out
+
+
+def gibbs_sweep(t: Target, s_prev, xi):
+    """One reparameterised Gibbs sweep of the schools model (Section 3.1, Appendix B.1).
+    Returns (next state, its Jacobian d next / d s_prev)."""
+    s_prev, xi = _arr(s_prev), _arr(xi)
+    out = np.zeros(t.D)
+    J = np.zeros((t.D, t.D))
+    _load().o_gibbs_sweep(C.byref(t._c), _ptr(s_prev), _ptr(xi), _ptr(out), _ptr(J))
+    return out, J
 
 
 def f(p: Problem, t: int, s_prev):

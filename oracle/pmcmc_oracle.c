@@ -8,8 +8,9 @@
  * It is a plain, slow, sequential restatement of what the paper's samplers compute:
  *   - targets: Gaussian, Bayesian logistic regression, 2-D banana (log p, gradient, Hessian);
  *   - transitions f_t: MALA (Section 3.2), HMC with a sequential leapfrog (Algorithm 2), one
- *     leapfrog step on [x, v] (Eq. 7), and MALA without the MH correction (ULA, for the affine
- *     special case of Section 2);
+ *     leapfrog step on [x, v] (Eq. 7), MALA without the MH correction (ULA, for the affine
+ *     special case of Section 2), and the reparameterised Gibbs sweep of the hierarchical
+ *     Gaussian model (Section 3.1, Appendix B.1);
  *   - the sequential chain s_t = f_t(s_{t-1}) (Section 2), which is the exact answer;
  *   - the Newton Jacobians: the stop-gradient relaxation of the accept/reject gate
  *     (Section 3.2), its diagonal (quasi-DEER, Eq. 4), the leapfrog Jacobian (Eq. 8) and its
@@ -30,11 +31,13 @@
 #define OT_GAUSSIAN 0
 #define OT_LOGREG 1
 #define OT_BANANA 2
+#define OT_SCHOOLS 3
 
 #define OS_MALA 0
 #define OS_HMC 1
 #define OS_LEAPFROG 2
 #define OS_ULA 3
+#define OS_GIBBS 4
 
 #define OJ_DENSE 0
 #define OJ_DIAG 1
@@ -44,7 +47,7 @@
 typedef struct {
     int kind, D, N;
     const double *mu, *P; /* Gaussian N(mu, P^-1): mean (D), precision (D*D) */
-    const double *X, *y;  /* logistic regression: design N*D, labels N */
+    const double *X, *y;  /* logistic regression: design N*D, labels N; schools: scores S*N */
     double sigma_p;       /* logistic regression prior N(0, sigma_p^2 I) */
 } o_target;
 
@@ -280,6 +283,105 @@ void o_leapfrog(const o_target *tg, double eps, const double *s, double *out) {
     free(g);
 }
 
+/*
+ * Reparameterised Gibbs sweep of the hierarchical Gaussian ("eight schools") model of the Gibbs
+ * experiment (Section 3.1, Eq. 5-6; the model, its hyperparameters and the coordinate order are
+ * those of Appendix B.1).  S schools with N scores each, X[s*N + n]; state
+ *   s = (tau^2, mu, theta_1..theta_S, sigma^2_1..sigma^2_S),  D = 2 + 2S.
+ * Model: tau^2 ~ Inv-chi^2(nu0, tau0^2), mu | tau^2 ~ N(mu0, tau^2 / kappa0),
+ * theta_s | mu, tau^2 ~ N(mu, tau^2), sigma^2_s ~ Inv-chi^2(alpha0, sigma0^2),
+ * x_sn | theta_s, sigma^2_s ~ N(theta_s, sigma^2_s)  (Inv-chi^2 = scaled inverse chi-square).
+ * Conjugacy gives the conditionals used in order:
+ *   tau^2   | mu, theta            Inv-chi^2(nu0 + S + 1, A / (nu0 + S + 1)),
+ *                                  A = nu0 tau0^2 + kappa0 (mu - mu0)^2 + sum_s (theta_s - mu)^2;
+ *   mu      | theta, tau^2         N((kappa0 mu0 + sum_s theta_s) / (kappa0 + S), tau^2 / (kappa0 + S));
+ *   theta_s | mu, tau^2, sigma^2_s N(m_s, 1 / P_s),  P_s = 1 / tau^2 + N / sigma^2_s,
+ *                                  m_s = (mu / tau^2 + sum_n x_sn / sigma^2_s) / P_s;
+ *   sigma^2_s | theta_s            Inv-chi^2(alpha0 + N, B_s / (alpha0 + N)),
+ *                                  B_s = alpha0 sigma0^2 + sum_n (x_sn - theta_s)^2;
+ * tau^2 and mu use the previous sweep's theta and mu, theta_s the previous sigma^2_s, so the sweep
+ * does not depend on the previous tau^2 (Eq. 6).  Reparameterisation: the noise xi (D values) holds
+ * xi[0] ~ Inv-chi^2(nu0 + S + 1, 1), xi[1] and xi[2 + s] ~ N(0, 1), xi[2 + S + s] ~
+ * Inv-chi^2(alpha0 + N, 1); an Inv-chi^2(nu, 1) variate times c is Inv-chi^2(nu, c) (Appendix B.1),
+ * a standard normal times sd plus mean is N(mean, sd^2).
+ * J (may be NULL): the D x D Jacobian d out / d s_prev, row by row in the order of the updates
+ * (forward-mode chain rule through the sweep).
+ * Pinned by: each conditional's draws against scipy's distributions (tests/test_oracle.py),
+ * finite differences of J, zero first column of J.
+ */
+#define SCH_NU0 0.1
+#define SCH_TAU0SQ 100.0
+#define SCH_MU0 0.0
+#define SCH_KAPPA0 0.1
+#define SCH_ALPHA0 0.1
+#define SCH_SIGMA0SQ 10.0
+
+void o_gibbs_sweep(const o_target *tg, const double *sp, const double *xi, double *out, double *J) {
+    int D = tg->D, S = (D - 2) / 2, N = tg->N;
+    const double *X = tg->X;
+    double *dtau = dalloc(D), *dmu = dalloc(D), *dth = dalloc(D), *dP = dalloc(D), *da = dalloc(D);
+    double mu_p = sp[1];
+    /* tau^2 */
+    double nu_n = SCH_NU0 + S + 1, A = SCH_NU0 * SCH_TAU0SQ + SCH_KAPPA0 * (mu_p - SCH_MU0) * (mu_p - SCH_MU0);
+    double sum_dev = 0.0, sum_th = 0.0;
+    for (int k = 0; k < S; k++) {
+        double dv = sp[2 + k] - mu_p;
+        A += dv * dv;
+        sum_dev += dv;
+        sum_th += sp[2 + k];
+    }
+    double tau2 = xi[0] * A / nu_n;
+    out[0] = tau2;
+    dtau[1] = xi[0] / nu_n * (2.0 * SCH_KAPPA0 * (mu_p - SCH_MU0) - 2.0 * sum_dev);
+    for (int k = 0; k < S; k++) dtau[2 + k] = xi[0] / nu_n * 2.0 * (sp[2 + k] - mu_p);
+    /* mu */
+    double kS = SCH_KAPPA0 + S;
+    double mu = (SCH_KAPPA0 * SCH_MU0 + sum_th) / kS + sqrt(tau2 / kS) * xi[1];
+    out[1] = mu;
+    double c_mu = xi[1] / (2.0 * sqrt(kS * tau2));
+    for (int j = 0; j < D; j++) dmu[j] = c_mu * dtau[j];
+    for (int k = 0; k < S; k++) dmu[2 + k] += 1.0 / kS;
+    if (J) {
+        for (int j = 0; j < D; j++) {
+            J[0 * D + j] = dtau[j];
+            J[1 * D + j] = dmu[j];
+        }
+    }
+    /* theta_s, then sigma^2_s */
+    for (int k = 0; k < S; k++) {
+        double sg = sp[2 + S + k], sx = 0.0;
+        for (int n = 0; n < N; n++) sx += X[(size_t)k * N + n];
+        double P = 1.0 / tau2 + N / sg;
+        double a = mu / tau2 + sx / sg;
+        double m = a / P;
+        double th = m + xi[2 + k] / sqrt(P);
+        out[2 + k] = th;
+        double B = SCH_ALPHA0 * SCH_SIGMA0SQ, dB = 0.0;
+        for (int n = 0; n < N; n++) {
+            double e = X[(size_t)k * N + n] - th;
+            B += e * e;
+            dB += -2.0 * e;
+        }
+        double an = SCH_ALPHA0 + N;
+        out[2 + S + k] = xi[2 + S + k] * B / an;
+        if (J) {
+            for (int j = 0; j < D; j++) {
+                dP[j] = -dtau[j] / (tau2 * tau2);
+                da[j] = dmu[j] / tau2 - mu * dtau[j] / (tau2 * tau2);
+            }
+            dP[2 + S + k] += -N / (sg * sg);
+            da[2 + S + k] += -sx / (sg * sg);
+            for (int j = 0; j < D; j++) {
+                double dm = da[j] / P - a * dP[j] / (P * P);
+                dth[j] = dm - 0.5 * xi[2 + k] * dP[j] / (P * sqrt(P));
+                J[(2 + k) * D + j] = dth[j];
+                J[(2 + S + k) * D + j] = xi[2 + S + k] / an * dB * dth[j];
+            }
+        }
+    }
+    free(dtau); free(dmu); free(dth); free(dP); free(da);
+}
+
 /* f_t(s_prev) for the problem's sampler; t is 1-based.  *ell: MALA log ratio / HMC H0-HL. */
 void o_f(const o_problem *pr, int t, const double *s_prev, double *out, double *ell, int *accept) {
     int D = pr->tgt.D;
@@ -289,6 +391,11 @@ void o_f(const o_problem *pr, int t, const double *s_prev, double *out, double *
     case OS_MALA: o_mala_step(&pr->tgt, pr->eps, s_prev, xi, u, 1, out, ell, accept); break;
     case OS_ULA: o_mala_step(&pr->tgt, pr->eps, s_prev, xi, u, 0, out, ell, accept); break;
     case OS_HMC: o_hmc_step(&pr->tgt, pr->eps, pr->L, s_prev, xi, u, out, ell, accept); break;
+    case OS_GIBBS:
+        o_gibbs_sweep(&pr->tgt, s_prev, xi, out, NULL);
+        if (ell) *ell = 0.0;
+        if (accept) *accept = 1;
+        break;
     default:
         o_leapfrog(&pr->tgt, pr->eps, s_prev, out);
         if (ell) *ell = 0.0;
@@ -464,6 +571,12 @@ void o_jac(const o_problem *pr, int t, const double *s_prev, int kind, double *J
     case OS_MALA: o_mala_jac(&pr->tgt, pr->eps, s_prev, xi, u, pr->gate_grad, J); break;
     case OS_HMC: o_hmc_jac(&pr->tgt, pr->eps, pr->L, s_prev, xi, u, pr->gate_grad, J); break;
     case OS_LEAPFROG: o_leapfrog_jac(&pr->tgt, pr->eps, s_prev, J); break;
+    case OS_GIBBS: {
+        double *tmp = dalloc(n);
+        o_gibbs_sweep(&pr->tgt, s_prev, xi, tmp, J);
+        free(tmp);
+        break;
+    }
     default: { /* ULA: I + eps H(x) */
         o_hess(&pr->tgt, s_prev, J);
         for (int i = 0; i < D * D; i++) J[i] *= pr->eps;

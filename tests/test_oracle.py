@@ -537,3 +537,136 @@ def test_linear_recursion_is_sum_of_products(dense):
                 M = (A[j] if dense else np.diag(A[j])) @ M
             ref += M @ b[k]
         np.testing.assert_allclose(got[t], ref, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------
+# Reparameterised Gibbs on the hierarchical Gaussian (schools) model (Section 3.1, App. B.1)
+# ------------------------------------------------------------------------------------------
+
+# hyperparameters stated in Appendix B.1
+_NU0, _TAU0SQ, _MU0, _KAPPA0, _ALPHA0, _SIGMA0SQ = 0.1, 100.0, 0.0, 0.1, 0.1, 10.0
+
+
+def _log_inv_chi2(v, nu, s2):
+    # scaled inverse chi-square(nu, s2) = inverse gamma(nu / 2, nu s2 / 2)
+    return stats.invgamma.logpdf(v, a=nu / 2.0, scale=nu * s2 / 2.0)
+
+
+def _schools_log_joint(tau2, mu, theta, sig2, X):
+    """log p(tau^2, mu, theta, sigma^2, X) of the generative model, term by term (scipy)."""
+    lp = _log_inv_chi2(tau2, _NU0, _TAU0SQ) + stats.norm.logpdf(mu, _MU0, np.sqrt(tau2 / _KAPPA0))
+    lp = lp + np.sum([stats.norm.logpdf(th, mu, np.sqrt(tau2)) for th in theta], axis=0)
+    lp = lp + np.sum([_log_inv_chi2(v, _ALPHA0, _SIGMA0SQ) for v in sig2], axis=0)
+    for s in range(X.shape[0]):
+        lp = lp + np.sum(stats.norm.logpdf(X[s][:, None], theta[s], np.sqrt(sig2[s])), axis=0)
+    return lp
+
+
+def _ks_against_density(draws, logdens, lo, hi, positive):
+    """KS distance between the draws and the distribution whose log density (up to a constant)
+    is logdens, integrated numerically on a fine grid over [lo, hi]."""
+    grid = np.geomspace(lo, hi, 40001) if positive else np.linspace(lo, hi, 40001)
+    lp = logdens(grid)
+    w = np.exp(lp - lp.max())
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (w[1:] + w[:-1]) * np.diff(grid))])
+    cdf /= cdf[-1]
+    x = np.sort(draws)
+    F = np.interp(x, grid, cdf)
+    n = len(x)
+    return max(np.max(np.arange(1, n + 1) / n - F), np.max(F - np.arange(n) / n))
+
+
+def test_gibbs_conditionals_match_the_joint_density():
+    """Each coordinate update of the sweep, with the coordinates it conditions on held fixed and
+    only its own noise varied, draws from the conditional that the model's joint density
+    (scipy, term by term) gives by numerical integration: tau^2 | previous (mu, theta); mu |
+    previous theta, new tau^2; theta_s | new (mu, tau^2), previous sigma^2_s; sigma^2_s | new
+    theta_s.  This pins the conditionals, the order of the sweep and the reparameterisation
+    noise (Inv-chi^2 base variates) together."""
+    S, N, M = 3, 5, 4000
+    X = W.schools_data(S, N, seed=4)
+    D = 2 + 2 * S
+    t = O.Target("schools", D, X=X)
+    sp = W.schools_init(X) * np.array([1.3, 1.0] + [1.0] * S + [0.8] * S) + \
+        np.array([0, 2.0] + [1.5] * S + [0] * S)
+    base = W.gibbs_noise(1, S, N, seed=9)[0]
+    pool = W.gibbs_noise(M, S, N, seed=10)
+    crit = 1.95 / np.sqrt(M)  # KS critical value at p ~ 0.001
+
+    def sweep_col(col, vary):
+        out = []
+        for m in range(M):
+            xi = base.copy()
+            xi[vary] = pool[m, vary]
+            out.append(O.gibbs_sweep(t, sp, xi)[0][col])
+        return np.array(out)
+
+    th_p, sg_p = sp[2:2 + S], sp[2 + S:]
+    fixed = O.gibbs_sweep(t, sp, base)[0]
+    tau2_t, mu_t = fixed[0], fixed[1]
+    # tau^2 | mu_{t-1}, theta_{t-1}
+    d = sweep_col(0, 0)
+    ks = _ks_against_density(d, lambda v: _schools_log_joint(v, sp[1], th_p, sg_p, X),
+                             d.min() * 0.5, d.max() * 3.0, True)
+    assert ks < crit, ("tau2", ks)
+    # mu | theta_{t-1}, tau^2_t
+    d = sweep_col(1, 1)
+    span = d.max() - d.min()
+    ks = _ks_against_density(d, lambda v: _schools_log_joint(tau2_t, v, th_p, sg_p, X),
+                             d.min() - span, d.max() + span, False)
+    assert ks < crit, ("mu", ks)
+    for s in range(S):
+        # theta_s | mu_t, tau^2_t, sigma^2_{s,t-1}
+        d = sweep_col(2 + s, 2 + s)
+        span = d.max() - d.min()
+
+        def lth(v, s=s):
+            th = [np.full_like(v, x) for x in th_p]
+            th[s] = v
+            return _schools_log_joint(tau2_t, mu_t, th, sg_p, X)
+        ks = _ks_against_density(d, lth, d.min() - span, d.max() + span, False)
+        assert ks < crit, ("theta", s, ks)
+        # sigma^2_s | theta_{s,t}
+        xi = base.copy()
+        theta_t = O.gibbs_sweep(t, sp, xi)[0][2:2 + S]
+        d = sweep_col(2 + S + s, 2 + S + s)
+
+        def lsg(v, s=s):
+            sg = [np.full_like(v, x) for x in sg_p]
+            sg[s] = v
+            return _schools_log_joint(tau2_t, mu_t, theta_t, sg, X)
+        ks = _ks_against_density(d, lsg, d.min() * 0.5, d.max() * 3.0, True)
+        assert ks < crit, ("sigma2", s, ks)
+
+
+def test_gibbs_jacobian_matches_finite_differences():
+    S, N = 4, 7
+    X = W.schools_data(S, N, seed=2)
+    D = 2 + 2 * S
+    t = O.Target("schools", D, X=X)
+    sp = W.schools_init(X)
+    xi = W.gibbs_noise(1, S, N, seed=3)[0]
+    _, J = O.gibbs_sweep(t, sp, xi)
+    Jfd = np.zeros((D, D))
+    for j in range(D):
+        h = 1e-6 * (1 + abs(sp[j]))
+        e = np.zeros(D)
+        e[j] = h
+        Jfd[:, j] = (O.gibbs_sweep(t, sp + e, xi)[0] - O.gibbs_sweep(t, sp - e, xi)[0]) / (2 * h)
+    np.testing.assert_allclose(J, Jfd, rtol=1e-6, atol=1e-8)
+    # the sweep does not read the previous tau^2 (Eq. 6)
+    assert np.all(J[:, 0] == 0.0)
+
+
+@pytest.mark.parametrize("jac", ["dense", "diag"])
+def test_gibbs_deer_reaches_sequential_trace(jac):
+    S, N, T = 8, 20, 64
+    X = W.schools_data(S, N)
+    p = O.Problem(O.Target("schools", 2 + 2 * S, X=X), "gibbs", 0.0,
+                  xi=W.gibbs_noise(T, S, N, seed=1), u=np.full(T, 0.5))
+    s0 = W.schools_init(X)
+    ref, _, acc = O.chain(p, T, s0)
+    assert acc.all()
+    s, iters, conv, _ = O.deer(p, T, s0, kind=jac, atol=1e-9, rtol=1e-12)
+    assert conv and iters <= T
+    np.testing.assert_allclose(s, ref, rtol=1e-8, atol=1e-8)

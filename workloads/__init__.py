@@ -15,6 +15,13 @@ Input recipe (all seeds default to 0; draws are taken in the order listed):
 * Sampler noise (Section 3.2 / Algorithm 2): ``xi_t ~ N(0, I_D)`` per step and
   ``u_t ~ U(0, 1)`` on the open interval, ``u = (k + 0.5) 2^-53`` with ``k`` a uniform 53-bit
   integer, so ``log u`` is always finite.
+* Hierarchical Gaussian ("eight schools") Gibbs workload (Section 5.1, Appendix B.1): S = 8
+  schools of N = 20 scores.  The paper matched its synthetic scores to a published table of
+  school means and standard errors; that table is not reproduced here.  Instead school means
+  ~ N(5, 10^2), school standard deviations ~ U(5, 20), scores = mean + sd * N(0, 1).  The Gibbs
+  noise per sweep is the reparameterisation input: an Inv-chi^2(nu0 + S + 1, 1) variate
+  (nu / chi^2_nu), 1 + S standard normals and S Inv-chi^2(alpha0 + N, 1) variates, with the
+  paper's nu0 = alpha0 = 0.1.
 """
 from __future__ import annotations
 
@@ -24,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "blr_data", "gaussian_c1", "random_spd", "noise", "Chain", "batched_mix",
-    "C1", "C2", "C3", "C4",
+    "schools_data", "schools_init", "gibbs_noise", "C1", "C2", "C3", "C4", "GIBBS",
 ]
 
 
@@ -76,6 +83,40 @@ def noise(T: int, D: int, seed: int = 0, dtype=np.float64):
     return xi.astype(dtype), u
 
 
+# degrees of freedom of the two scaled-inverse-chi-square priors of the schools model (App. B.1)
+SCHOOLS_NU0 = 0.1
+SCHOOLS_ALPHA0 = 0.1
+
+
+def schools_data(S: int = 8, N: int = 20, seed: int = 0, dtype=np.float64):
+    """Scores of S schools x N students (row s = school s)."""
+    rng = _rng(seed)
+    means = rng.normal(5.0, 10.0, S)
+    sds = rng.uniform(5.0, 20.0, S)
+    X = means[:, None] + sds[:, None] * rng.standard_normal((S, N))
+    return X.astype(dtype)
+
+
+def schools_init(X):
+    """A starting state from the data's moments: tau^2 = spread of the school means + 1,
+    mu = their mean, theta_s = school means, sigma^2_s = within-school variances."""
+    X = np.asarray(X, dtype=np.float64)
+    m = X.mean(axis=1)
+    return np.concatenate([[m.var(ddof=1) + 1.0, m.mean()], m, X.var(axis=1, ddof=1)])
+
+
+def gibbs_noise(T: int, S: int, N: int, seed: int = 0, dtype=np.float64):
+    """Per-sweep Gibbs noise, T x (2 + 2S), in the state's order (tau^2, mu, theta, sigma^2)."""
+    rng = _rng(seed)
+    nu_t = SCHOOLS_NU0 + S + 1
+    nu_s = SCHOOLS_ALPHA0 + N
+    xi = np.empty((T, 2 + 2 * S))
+    xi[:, 0] = nu_t / rng.chisquare(nu_t, T)
+    xi[:, 1:2 + S] = rng.standard_normal((T, 1 + S))
+    xi[:, 2 + S:] = nu_s / rng.chisquare(nu_s, (T, S))
+    return xi.astype(dtype)
+
+
 # --------------------------------------------------------------------------------------------
 # Named workloads (sizes as the benchmark configurations state them)
 # --------------------------------------------------------------------------------------------
@@ -110,6 +151,12 @@ C3 = Workload("hmc_banana_l16_t100000", "hmc", "banana", T=100000, D=2, L=16, st
 # about 80% acceptance (Appendix B.1): 5e-4 gives 82% on this synthetic data.
 C4 = Workload("mala_logreg_n5000_d100_t65536", "mala", "logreg", T=65536, D=100, N=5000,
               step=5e-4, tol=1e-5)
+
+
+# Reparameterised Gibbs on the schools model (Section 5.1): S = 8, N = 20, one chain of 2^17
+# sweeps, FP32 (the paper ran chains up to 1M sweeps, in batches of 1 to 64).
+GIBBS = Workload("gibbs_schools_s8_n20_t131072", "gibbs", "schools", T=131072, D=18, N=20,
+                 step=0.0, tol=1e-4, rtol=1e-5)
 
 
 @dataclass
