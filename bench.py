@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--workload", default="c2",
                     choices=["c2", "c1", "c3_diag", "c3_bf16", "c3_block", "c4", "c5",
+                             "gibbs_diag", "gibbs_dense",
                              "scan_sweep"],
                     help="c2 (default) is the headline line; the others measure the other "
                          "configurations")
@@ -479,6 +480,27 @@ def run_other(args):
         line.update(config=f"{c.name} {wl}", value=c.T / (ms / 1e3), ms_per_step=ms,
                     newton_iters=res["iters"], status=res["status"], accept_rate=res["accept_rate"],
                     dtype="f32", seq_gpu={"value": c.T / (sms / 1e3), "ms": sms, "speedup": sms / ms})
+    elif wl in ("gibbs_diag", "gibbs_dense"):
+        c = W.GIBBS
+        S = (c.D - 2) // 2
+        X = W.schools_data(S, c.N, seed=0, dtype=np.float32)
+        xi = W.gibbs_noise(c.T, S, c.N, seed=1, dtype=np.float32)
+        tgt = P.Target("schools", c.D, X=torch.tensor(X, device=dev))
+        s0 = torch.tensor(W.schools_init(X), dtype=torch.float32, device=dev)
+        xid = torch.tensor(xi, device=dev)
+        ud = torch.full((c.T,), 0.5, dtype=torch.float64, device=dev)
+        opt = P.Options(sampler="gibbs", jac="diag" if wl == "gibbs_diag" else "dense",
+                        precision="f32", atol=c.tol, rtol=c.rtol)
+        ms, (s, res) = _timed(lambda: P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud), args.steps,
+                              args.warmup, flush, stream, torch)
+        sopt = P.Options(sampler="gibbs", precision="f32")
+        sms, (sq, _) = _timed(lambda: P.pmcmc_seq_solve(tgt, sopt, c.T, s0, xid, ud), 1, 1, flush,
+                              stream, torch)
+        dev_max = float(((s - sq).abs() / (1 + sq.abs())).max().item())
+        line.update(config=f"{c.name} {wl}", value=c.T / (ms / 1e3), ms_per_step=ms,
+                    newton_iters=res["iters"], status=res["status"], dtype="f32",
+                    max_rel_dev_from_sequential=dev_max,
+                    seq_gpu={"value": c.T / (sms / 1e3), "ms": sms, "speedup": sms / ms})
     elif wl == "c4":
         c = W.C4
         X, y, _ = W.blr_data(c.N, c.D, seed=0, dtype=np.float32)

@@ -51,13 +51,27 @@ typedef enum {
 
 /* f_t: the sampler transition (Section 3.2 MALA; Algorithm 2 HMC with a sequential leapfrog;
  * HMC with the leapfrog itself solved by block quasi-DEER, Section 3.3). */
-typedef enum { PMCMC_MALA = 0, PMCMC_HMC = 1, PMCMC_HMC_PAR_LEAPFROG = 2 } pmcmc_sampler;
+typedef enum {
+    PMCMC_MALA = 0,
+    PMCMC_HMC = 1,
+    PMCMC_HMC_PAR_LEAPFROG = 2,
+    PMCMC_GIBBS = 3  /* reparameterised Gibbs sweep (Section 3.1) of the PMCMC_SCHOOLS model */
+} pmcmc_sampler;
 
 /* Built-in target densities (log p up to a constant):
  *   GAUSSIAN: -1/2 (x - mean)^T prec (x - mean)
  *   LOGREG:   sum_n [y_n z_n - log(1 + exp z_n)] - |x|^2 / (2 prior_scale^2),  z = X x
- *   BANANA:   -x1^2/200 - (x2 + 0.1 x1^2 - 10)^2 / 2   (D = 2) */
-typedef enum { PMCMC_GAUSSIAN = 0, PMCMC_LOGREG = 1, PMCMC_BANANA = 2 } pmcmc_target_kind;
+ *   BANANA:   -x1^2/200 - (x2 + 0.1 x1^2 - 10)^2 / 2   (D = 2)
+ *   SCHOOLS:  the hierarchical Gaussian model of the Gibbs experiment (Appendix B.1): S schools
+ *             of N scores (X: S x N, row s = school s), state (tau^2, mu, theta_1..S,
+ *             sigma^2_1..S), D = 2 + 2S, 1 <= S <= 15, hyperparameters nu0 = 0.1,
+ *             tau0^2 = 100, mu0 = 0, kappa0 = 0.1, alpha0 = 0.1, sigma0^2 = 10.  Sampled by
+ *             PMCMC_GIBBS only.  The sweep's noise xi_t (D values, in the state's order) is the
+ *             reparameterisation input: xi[0] an Inv-chi^2(nu0 + S + 1, 1) variate, xi[1] and
+ *             xi[2 + s] standard normals, xi[2 + S + s] Inv-chi^2(alpha0 + N, 1) variates (the
+ *             caller draws them; the seed-driven generator makes only normals and uniforms).
+ *             u is not used.  step is not used. */
+typedef enum { PMCMC_GAUSSIAN = 0, PMCMC_LOGREG = 1, PMCMC_BANANA = 2, PMCMC_SCHOOLS = 3 } pmcmc_target_kind;
 
 /* Newton Jacobian used in step (a):
  *   DENSE      the full stop-gradient Jacobian (DEER, Eq. 2);
@@ -82,10 +96,10 @@ typedef enum { PMCMC_F64 = 0, PMCMC_F32 = 1, PMCMC_F32_SCAN_BF16 = 2 } pmcmc_pre
 typedef struct {
     pmcmc_target_kind kind;
     int D;               /* dimension of x */
-    int N;               /* LOGREG: number of rows of X */
+    int N;               /* LOGREG: number of rows of X; SCHOOLS: scores per school */
     const void *mean;    /* GAUSSIAN: D reals, device */
     const void *prec;    /* GAUSSIAN: D x D precision matrix (symmetric), row-major, device */
-    const void *X;       /* LOGREG: N x D design, row-major, device */
+    const void *X;       /* LOGREG: N x D design, row-major, device; SCHOOLS: S x N scores */
     const void *y;       /* LOGREG: N labels in {0, 1}, reals, device */
     double prior_scale;  /* LOGREG: prior N(0, prior_scale^2 I) */
     const void *Q;       /* optional D x D orthogonal basis, row-major, device; the Newton solve

@@ -82,7 +82,10 @@ def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
 
 @dataclass
 class Target:
-    """A built-in target (include/pmcmc.h pmcmc_target); tensors live on the GPU."""
+    """A built-in target (include/pmcmc.h pmcmc_target); tensors live on the GPU.
+
+    kind "schools": X holds the S x N scores of the hierarchical Gaussian model sampled by the
+    "gibbs" sampler, D = 2 + 2 S."""
     kind: str
     D: int
     mean: torch.Tensor | None = None
@@ -96,7 +99,7 @@ class Target:
         self._keep = [_dev(t, dtype, n) for t, n in ((self.mean, "mean"), (self.prec, "prec"),
                                                     (self.X, "X"), (self.y, "y"), (self.Q, "Q"))]
         m, p, x, y, q = self._keep
-        N = 0 if x is None else x.shape[0]
+        N = 0 if x is None else (x.shape[1] if self.kind == "schools" else x.shape[0])
         return L.pmcmc_target(TARGETS[self.kind], self.D, N, _ptr(m), _ptr(p), _ptr(x), _ptr(y),
                               float(self.prior_scale), _ptr(q))
 

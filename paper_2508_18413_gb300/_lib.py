@@ -13,8 +13,8 @@ PMCMC_EINVAL, PMCMC_ENOMEM, PMCMC_ECUDA, PMCMC_ETIMEOUT, PMCMC_ENAN, PMCMC_EUNSU
     -1, -2, -3, -4, -5, -6)
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA",
                 -4: "ETIMEOUT", -5: "ENAN", -6: "EUNSUPPORTED"}
-SAMPLERS = {"mala": 0, "hmc": 1, "hmc_par_leapfrog": 2}
-TARGETS = {"gaussian": 0, "logreg": 1, "banana": 2}
+SAMPLERS = {"mala": 0, "hmc": 1, "hmc_par_leapfrog": 2, "gibbs": 3}
+TARGETS = {"gaussian": 0, "logreg": 1, "banana": 2, "schools": 3}
 JACS = {"dense": 0, "diag": 1, "block2": 2, "diag_hutch": 3, "zero": 4}
 PRECISIONS = {"f64": 0, "f32": 1, "f32_scan_bf16": 2}
 ENGINES = {"auto": 0, "simt": 1}

@@ -56,6 +56,10 @@ struct EvalArgs {
 };
 
 cudaError_t launch_eval_small(const EvalArgs &A, cudaStream_t st);
+// reparameterised Gibbs on the schools target (eval_gibbs.cu): R arithmetic, S pair storage
+bool gibbs_supported(int D, int N);
+template <typename R, typename S>
+cudaError_t launch_gibbs(const EvalArgs &A, cudaStream_t st, bool seq);
 cudaError_t launch_seq_small(const EvalArgs &A, cudaStream_t st);
 cudaError_t launch_eval_logreg(const EvalArgs &A, cudaStream_t st);
 cudaError_t launch_seq_logreg(const EvalArgs &A, cudaStream_t st);

@@ -487,6 +487,7 @@ cudaError_t dispatch_dm(const EvalArgs &A, cudaStream_t st, bool seq) {
 
 template <typename R, typename S>
 cudaError_t dispatch_ts(const EvalArgs &A, cudaStream_t st, bool seq) {
+    if (A.sampler == PMCMC_GIBBS) return launch_gibbs<R, S>(A, st, seq);
     if (A.target == PMCMC_GAUSSIAN) {
         if (A.sampler == PMCMC_MALA) return dispatch_dm<R, S, PMCMC_GAUSSIAN, PMCMC_MALA>(A, st, seq);
         return dispatch_dm<R, S, PMCMC_GAUSSIAN, PMCMC_HMC>(A, st, seq);

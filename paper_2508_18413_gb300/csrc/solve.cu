@@ -320,9 +320,12 @@ pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opt
     if (T < 0) return fail(c, PMCMC_EINVAL, "T must be >= 0");
     const int D = tg->D;
     if (D <= 0) return fail(c, PMCMC_EINVAL, "D must be > 0");
-    if (!(o->step > 0.0)) return fail(c, PMCMC_EINVAL, "step must be > 0");
-    if (o->sampler != PMCMC_MALA && o->sampler != PMCMC_HMC && o->sampler != PMCMC_HMC_PAR_LEAPFROG)
+    if (o->sampler != PMCMC_MALA && o->sampler != PMCMC_HMC && o->sampler != PMCMC_HMC_PAR_LEAPFROG &&
+        o->sampler != PMCMC_GIBBS)
         return fail(c, PMCMC_EINVAL, "unknown sampler");
+    if (o->sampler != PMCMC_GIBBS && !(o->step > 0.0)) return fail(c, PMCMC_EINVAL, "step must be > 0");
+    if ((o->sampler == PMCMC_GIBBS) != (tg->kind == PMCMC_SCHOOLS))
+        return fail(c, PMCMC_EINVAL, "PMCMC_GIBBS runs on (only) the PMCMC_SCHOOLS target");
     if ((o->sampler == PMCMC_HMC || o->sampler == PMCMC_HMC_PAR_LEAPFROG) && o->leapfrog_L < 1)
         return fail(c, PMCMC_EINVAL, "HMC needs leapfrog_L >= 1");
     if (o->precision < PMCMC_F64 || o->precision > PMCMC_F32_SCAN_BF16)
@@ -336,6 +339,14 @@ pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opt
         break;
     case PMCMC_BANANA:
         if (D != 2) return fail(c, PMCMC_EINVAL, "banana target has D = 2");
+        break;
+    case PMCMC_SCHOOLS:
+        if (!tg->X || tg->N <= 0) return fail(c, PMCMC_EINVAL, "schools needs X (S x N scores), N > 0");
+        if (!gibbs_supported(D, tg->N))
+            return fail(c, PMCMC_EUNSUPPORTED, "schools target has D = 2 + 2 S with 1 <= S <= 15");
+        if (tg->Q) return fail(c, PMCMC_EUNSUPPORTED, "no basis reparameterisation for Gibbs");
+        if (o->jac != PMCMC_JAC_DENSE && o->jac != PMCMC_JAC_DIAG && o->jac != PMCMC_JAC_ZERO)
+            return fail(c, PMCMC_EUNSUPPORTED, "Gibbs supports DENSE, DIAG and ZERO Jacobians");
         break;
     case PMCMC_LOGREG:
         if (!tg->X || !tg->y || tg->N <= 0) return fail(c, PMCMC_EINVAL, "logreg needs X, y, N > 0");
@@ -456,6 +467,8 @@ extern "C" pmcmc_status pmcmc_solve(pmcmc_ctx *c, const pmcmc_target *tg,
     if (ps != PMCMC_OK) return ps;
     if (T > 0 && !s_out) return fail(c, PMCMC_EINVAL, "s_out is NULL");
     if ((xi == nullptr) != (u == nullptr)) return fail(c, PMCMC_EINVAL, "pass both xi and u, or neither");
+    if (o->sampler == PMCMC_GIBBS && !xi)
+        return fail(c, PMCMC_EINVAL, "Gibbs needs xi (its reparameterisation noise) and u");
     if (T == 0) {
         if (res) res->status = PMCMC_OK;
         return PMCMC_OK;

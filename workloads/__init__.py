@@ -156,7 +156,7 @@ C4 = Workload("mala_logreg_n5000_d100_t65536", "mala", "logreg", T=65536, D=100,
 # Reparameterised Gibbs on the schools model (Section 5.1): S = 8, N = 20, one chain of 2^17
 # sweeps, FP32 (the paper ran chains up to 1M sweeps, in batches of 1 to 64).
 GIBBS = Workload("gibbs_schools_s8_n20_t131072", "gibbs", "schools", T=131072, D=18, N=20,
-                 step=0.0, tol=1e-4, rtol=1e-5)
+                 step=0.0, tol=1e-5, rtol=1e-6)
 
 
 @dataclass
