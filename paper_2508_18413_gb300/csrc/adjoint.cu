@@ -553,6 +553,7 @@ extern "C" pmcmc_status pmcmc_adjoint(pmcmc_ctx *c, const pmcmc_target *tg,
     // 64 < D <= 128, FP32: the J's are formed on the tensor cores from an image of X^T
     const bool hess_tc = !gauss && !f64 && o->engine != 1 && hess_tc_supported(D, tg->N);
     const size_t o_img = hess_tc ? cv.take(hess_tc_image_bytes(tg->N)) : 0;
+    const size_t o_w = hess_tc ? cv.take(sizeof(float) * hess_tc_w_floats((int)jslots, tg->N)) : 0;
     pmcmc_status ps = ws_reserve(c, cv.used);
     if (ps != PMCMC_OK) return ps;
     char *base = (char *)c->ws;
@@ -596,8 +597,9 @@ extern "C" pmcmc_status pmcmc_adjoint(pmcmc_ctx *c, const pmcmc_target *tg,
         for (int i = 0; i < cnt; i++) jmap[accepted[first + i] - t_lo - 1] = i;
         PM_CUDA_A(cudaMemcpyAsync(jmap_d, jmap.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
         if (hess_tc && cnt > 0) {
-            PM_CUDA_A(launch_hess_logreg_tc(cnt, list_d + first, D, tg->N, base + o_img,
-                                            (const float *)s0, (const float *)s, (float)eps,
+            PM_CUDA_A(launch_hess_logreg_tc(cnt, list_d + first, D, tg->N, (const float *)tg->X,
+                                            base + o_img, (const float *)s0, (const float *)s,
+                                            (float *)(base + o_w), (float)eps,
                                             (float)(1.0 / (sp * sp)), (float *)Jbuf,
                                             &c->ctl->scan.timeout, spin, st));
         } else if (!gauss && cnt > 0) {

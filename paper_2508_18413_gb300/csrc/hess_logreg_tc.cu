@@ -41,7 +41,9 @@ constexpr int kNB = 32;                  // data rows per K-chunk
 constexpr int kTile = kM * kNB * 4;      // one 128 x 32 tf32 operand: 16384 bytes
 constexpr int kChunk = 2 * kTile;        // image chunk: X^T hi, X^T lo
 constexpr int kStages = 4;
-constexpr int kPeriod = 1;               // chunks per TMEM accumulator before it is drained
+constexpr int kWBytes = 2 * kNB * 4;      // w of the chunk's 32 rows for both steps
+constexpr int kStageStride = 33 * 1024;  // image chunk + w, 1024-aligned
+constexpr int kPeriod = 4;               // chunks per TMEM accumulator before it is drained
 constexpr int kWorkWarps = 16, kWorkThreads = 32 * kWorkWarps;
 constexpr int kIssWarp = kWorkWarps, kCopyWarp = kWorkWarps + 1;
 constexpr int kThreads = 32 * (kWorkWarps + 2);
@@ -51,19 +53,18 @@ constexpr unsigned int kDrainLimit = 1u << 20;
 
 // shared-memory map (offsets from a 1024-aligned base)
 constexpr int oStage = 0;
-constexpr int oB = oStage + kStages * kChunk;     // B hi (256 rows), then B lo
-constexpr int oXs = oB + 4 * kTile;               // float [2][128]: the two states
-constexpr int oZp = oXs + 2 * kM * 4;             // float [2][8][32]: partial z
-constexpr int oW = oZp + 2 * 8 * kNB * 4;         // float [2][32]: w of the chunk
+constexpr int oB = oStage + kStages * kStageStride;  // B hi (256 rows), then B lo
 constexpr int bFull = 0, bEmpty = kStages, bBready = 2 * kStages, bBfree = bBready + 2,
               bAccFull = bBfree + 2, bAccEmpty = bAccFull + 2, bFin = bAccEmpty + 2,
               kNumBars = bFin + 1;
-constexpr int oBar = oW + 2 * kNB * 4;
+constexpr int oBar = oB + 4 * kTile;
 constexpr int oMisc = oBar + 8 * kNumBars;        // tmem address, abort flag
 constexpr int kSmemUsed = oMisc + 16;
 constexpr int kSmemBytes = kSmemUsed + 1024;      // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
-static_assert(oB % 1024 == 0 && kChunk % 1024 == 0 && oBar % 8 == 0, "alignment");
+static_assert(oB % 1024 == 0 && kStageStride % 1024 == 0 && kChunk + kWBytes <= kStageStride &&
+                  oBar % 8 == 0,
+              "alignment");
 
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort,
                                           unsigned int limit) {
@@ -96,11 +97,64 @@ __global__ void hess_tc_pack_kernel(const float *__restrict__ X, int N, int D, i
     *reinterpret_cast<float *>(base + kTile + off) = x - hi;  // exact: hi + lo = x
 }
 
+// W[g][n] = sigmoid'(X[n] . x_g) for the listed steps g (x_g = s_{list[g] - 1}, s0 for step 0)
+// and n < ldw (zero for n >= N): a 64-step x 64-row tile per CTA, features in slices of 32
+// through shared memory, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) hess_w_kernel(int nlist, const int *__restrict__ list, int D,
+                                                     int N, int ldw, const float *__restrict__ X,
+                                                     const float *__restrict__ s0,
+                                                     const float *__restrict__ s, float *__restrict__ W) {
+    __shared__ float xs[64][33], xr[64][33];
+    const int g0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float acc[4][4] = {};
+    for (int d0 = 0; d0 < D; d0 += 32) {
+        __syncthreads();
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int r = e >> 5, d = d0 + (e & 31);
+            const int g = g0 + r, n = n0 + r;
+            float v = 0.0f;
+            if (g < nlist && d < D) {
+                const int t = list[g];
+                v = t == 0 ? s0[d] : s[(size_t)(t - 1) * D + d];
+            }
+            xs[r][e & 31] = v;
+            xr[r][e & 31] = (n < N && d < D) ? X[(size_t)n * D + d] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int d = 0; d < 32; d++) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                a[i] = xs[4 * ty + i][d];
+                b[i] = xr[4 * tx + i][d];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int g = g0 + 4 * ty + i;
+        const int n = n0 + 4 * tx;
+        if (g >= nlist || n >= ldw) continue;
+        float w4[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float sg = 1.0f / (1.0f + expf(-acc[i][j]));
+            w4[j] = n + j < N ? sg * (1.0f - sg) : 0.0f;
+        }
+        *reinterpret_cast<float4 *>(W + (size_t)g * ldw + n) = make_float4(w4[0], w4[1], w4[2], w4[3]);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
-hess_logreg_tc_kernel(int nlist, const int *__restrict__ list, int D, int N,
-                      const unsigned char *__restrict__ img, const float *__restrict__ s0,
-                      const float *__restrict__ s, float eps, float inv_sp2, float *__restrict__ Jbuf,
-                      unsigned int *timeout, unsigned int limit) {
+hess_logreg_tc_kernel(int nlist, int D, int N, const unsigned char *__restrict__ img,
+                      const float *__restrict__ W, int ldw, float eps, float inv_sp2,
+                      float *__restrict__ Jbuf, unsigned int *timeout, unsigned int limit) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -142,8 +196,13 @@ hess_logreg_tc_kernel(int nlist, const int *__restrict__ list, int D, int N,
                     if (k >= kStages &&
                         !(ok = mbar_wait(bar(bEmpty + st), (uint32_t)((k / kStages) - 1) & 1u, abort_f, limit)))
                         break;
-                    mbar_arrive_expect_tx(bar(bFull + st), kChunk);
-                    bulk_g2s(sb + oStage + st * kChunk, img + (size_t)c * kChunk, kChunk, bar(bFull + st));
+                    const uint32_t dst = sb + oStage + st * kStageStride;
+                    const int g0 = 2 * pr, g1 = 2 * pr + 1 < nlist ? 2 * pr + 1 : 2 * pr;
+                    mbar_arrive_expect_tx(bar(bFull + st), kChunk + kWBytes);
+                    bulk_g2s(dst, img + (size_t)c * kChunk, kChunk, bar(bFull + st));
+                    bulk_g2s(dst + kChunk, W + (size_t)g0 * ldw + (size_t)c * kNB, kWBytes / 2, bar(bFull + st));
+                    bulk_g2s(dst + kChunk + kWBytes / 2, W + (size_t)g1 * ldw + (size_t)c * kNB, kWBytes / 2,
+                             bar(bFull + st));
                 }
             }
             // copies still in flight complete on their own: wait for them before the CTA exits
@@ -165,7 +224,7 @@ hess_logreg_tc_kernel(int nlist, const int *__restrict__ list, int D, int N,
                     const int st = k % kStages;
                     if (!(ok = mbar_wait(bar(bFull + st), (uint32_t)(k / kStages) & 1u, abort_f, limit))) break;
                     const uint32_t acc = tm + (uint32_t)(p & 1) * 256u;
-                    const uint32_t a0 = sb + oStage + st * kChunk;
+                    const uint32_t a0 = sb + oStage + st * kStageStride;
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         if (!(ok = mbar_wait(bar(bBready + h), (uint32_t)k & 1u, abort_f, limit))) break;
@@ -195,25 +254,19 @@ hess_logreg_tc_kernel(int nlist, const int *__restrict__ list, int D, int N,
         const int i_row = 32 * q + lane;               // row i of H held by this thread
         const int u_out = cg >> 1, j0 = (cg & 1) * 64; // its step and first column j
         const uint32_t lrow = tm + ((uint32_t)(32 * q) << 16) + (uint32_t)(cg * 64);
-        float *xs = reinterpret_cast<float *>(sm + oXs);
-        float *zp = reinterpret_cast<float *>(sm + oZp);
-        float *wv = reinterpret_cast<float *>(sm + oW);
-        // Named barriers among the worker warps are never skipped by a subset of them: a failed
-        // wait marks the warp's status, the next and-barrier makes the status common to all
-        // workers, and only then do they leave together.
+        // Named barriers among the worker warps are never skipped by a subset of them: the
+        // chunk loop has none, a failed wait only marks the warp's status, and the and-barrier
+        // at the end of each pair makes the status common before the workers leave together.
+        // B positions of this thread (fixed for every chunk): lane -> (row, chunk) so that each
+        // quarter-warp covers two rows whose swizzled chunks fill all 32 banks (rows 8g + q and
+        // 8g + q + 4, chunk lane % 4 of the half); two positions per half, rows < 128 -> step 0
+        const int f_row0 = 8 * (tid >> 5) + ((lane >> 3) + 4 * ((lane >> 2) & 1));
+        const int f_row1 = f_row0 + 8 * (kWorkThreads >> 5);
+        const int f_u0 = f_row0 >> 7, f_u1 = f_row1 >> 7;
+        const uint32_t f_off0 = swz128((uint32_t)(f_row0 & (kM - 1)), (uint32_t)(4 * (lane & 3)));
+        const uint32_t f_off1 = swz128((uint32_t)(f_row1 & (kM - 1)), (uint32_t)(4 * (lane & 3)));
         int k = 0, gp = 0;
         for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
-            // the previous pair's readers of xs passed the and-barrier that ended that pair
-            if (tid < 2 * kM) {
-                const int u = tid / kM, i = tid % kM, g = 2 * pr + u;
-                float v = 0.0f;
-                if (g < nlist && i < D) {
-                    const int t = list[g];
-                    v = t == 0 ? s0[i] : s[(size_t)(t - 1) * D + i];
-                }
-                xs[tid] = v;
-            }
-            named_bar(1, kWorkThreads);
             float acc[64];
 #pragma unroll
             for (int e = 0; e < 64; e++) acc[e] = 0.0f;
@@ -224,59 +277,34 @@ hess_logreg_tc_kernel(int nlist, const int *__restrict__ list, int D, int N,
                 tc_fence_after();
                 const uint32_t a = lrow + (uint32_t)(p & 1) * 256u;
 #pragma unroll
-                for (int b4 = 0; b4 < 4; b4++) {
-                    float v[16];
-                    tmem_ld16(a + 16u * b4, v);
+                for (int b8 = 0; b8 < 8; b8++) {
+                    float v[8];
+                    tmem_ld8(a + 8u * b8, v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 16; e++) acc[16 * b4 + e] += v[e];
+                    for (int e = 0; e < 8; e++) acc[8 * b8 + e] += v[e];
                 }
                 warp_arrive(bar(bAccEmpty + (p & 1)));
                 return true;
             };
-            bool all_ok = true;
             for (int c = 0; c < nch; c++, k++) {
                 const int st = k % kStages;
-                const unsigned char *stg = sm + oStage + st * kChunk;
-                good = good && warp_wait(bar(bFull + st), (uint32_t)(k / kStages) & 1u, abort_f, limit);
-                // partial z of (step u, row n) over 16 features: warp -> (u, slice), lane -> n
-                if (good) {
-                    const int u = warp >> 3, sl = warp & 7;
-                    float part = 0.0f;
-#pragma unroll
-                    for (int r = 0; r < 16; r++) {
-                        const int i = 16 * sl + r;
-                        const uint32_t off = swz128((uint32_t)i, (uint32_t)lane);
-                        const float x = *reinterpret_cast<const float *>(stg + off) +
-                                        *reinterpret_cast<const float *>(stg + kTile + off);
-                        part = fmaf(x, xs[u * kM + i], part);
-                    }
-                    zp[(u * 8 + sl) * kNB + lane] = part;
-                }
-                if (!(all_ok = named_bar_and(1, kWorkThreads, good))) break;
-                if (tid < 2 * kNB) {
-                    const int u = tid / kNB, n = tid % kNB;
-                    float z = 0.0f;
-#pragma unroll
-                    for (int sl = 0; sl < 8; sl++) z += zp[(u * 8 + sl) * kNB + n];
-                    const float sg = 1.0f / (1.0f + expf(-z));
-                    wv[tid] = (c * kNB + n < N) ? sg * (1.0f - sg) : 0.0f;
-                }
-                named_bar(1, kWorkThreads);
+                const unsigned char *stg = sm + oStage + st * kStageStride;
+                if (good) good = warp_wait(bar(bFull + st), (uint32_t)(k / kStages) & 1u, abort_f, limit);
+                const float *wc = reinterpret_cast<const float *>(stg + kChunk);  // w of both steps
                 // B = w (.) X^T for both steps; half h = K-steps 2h, 2h + 1 (16-byte chunks 4h..4h+3)
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
                     if (good && k >= 1) good = warp_wait(bar(bBfree + h), (uint32_t)(k - 1) & 1u, abort_f, limit);
                     if (!good) continue;
-#pragma unroll
+#pragma unroll 1
                     for (int rep = 0; rep < 2; rep++) {
-                        const int pos = tid + rep * kWorkThreads;  // 0 .. 1023
-                        const int row = pos >> 2, c4 = 4 * h + (pos & 3);
-                        const int u = row >> 7, j = row & (kM - 1);
-                        const uint32_t off = swz128((uint32_t)j, (uint32_t)(4 * c4));
+                        // half h uses the chunk 4 further along: swizzled offset bit 6 flips
+                        const uint32_t off = (rep ? f_off1 : f_off0) ^ ((uint32_t)h << 6);
+                        const int u = rep ? f_u1 : f_u0;
                         const float4 xh = *reinterpret_cast<const float4 *>(stg + off);
                         const float4 xl = *reinterpret_cast<const float4 *>(stg + kTile + off);
-                        const float4 w4 = *reinterpret_cast<const float4 *>(wv + u * kNB + 4 * c4);
+                        const float4 w4 = *reinterpret_cast<const float4 *>(wc + u * kNB + 16 * h + 4 * (lane & 3));
                         float v[4] = {w4.x * (xh.x + xl.x), w4.y * (xh.y + xl.y), w4.z * (xh.z + xl.z),
                                       w4.w * (xh.w + xl.w)};
                         float hv[4], lv[4];
@@ -294,9 +322,9 @@ hess_logreg_tc_kernel(int nlist, const int *__restrict__ list, int D, int N,
                 // the previous period's accumulator completes behind this chunk's queued MMAs
                 if (good && c > 0 && (c % kPeriod) == 0) good = drain(gp + c / kPeriod - 1);
             }
-            if (all_ok && good) good = drain(gp + nper - 1);
+            if (good) good = drain(gp + nper - 1);
             gp += nper;
-            if (!named_bar_and(1, kWorkThreads, all_ok && good)) break;
+            if (!named_bar_and(1, kWorkThreads, good)) break;
             // J_u = I + eps H_u; H is symmetric, so row i of this thread's result is written as
             // column i (consecutive lanes -> consecutive addresses)
             const int g = 2 * pr + u_out;
@@ -324,6 +352,8 @@ hess_logreg_tc_kernel(int nlist, const int *__restrict__ list, int D, int N,
 
 bool hess_tc_supported(int D, int N) { return D > 64 && D <= kM && N > 0; }
 
+size_t hess_tc_w_floats(int nlist, int N) { return (size_t)nlist * (size_t)((N + kNB - 1) / kNB * kNB); }
+
 size_t hess_tc_image_bytes(int N) { return (size_t)((N + kNB - 1) / kNB) * kChunk; }
 
 cudaError_t launch_hess_tc_pack(const float *X, int N, int D, void *img, cudaStream_t st) {
@@ -334,12 +364,17 @@ cudaError_t launch_hess_tc_pack(const float *X, int N, int D, void *img, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_hess_logreg_tc(int nlist, const int *list, int D, int N, const void *img,
-                                  const float *s0, const float *s, float eps, float inv_sp2,
-                                  float *Jbuf, unsigned int *timeout, unsigned int spin_limit,
-                                  cudaStream_t st) {
+cudaError_t launch_hess_logreg_tc(int nlist, const int *list, int D, int N, const float *X,
+                                  const void *img, const float *s0, const float *s, float *W,
+                                  float eps, float inv_sp2, float *Jbuf, unsigned int *timeout,
+                                  unsigned int spin_limit, cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
-    cudaError_t e = ensure_dyn_smem(hess_logreg_tc_kernel, kSmemBytes);
+    const int ldw = (N + kNB - 1) / kNB * kNB;
+    hess_w_kernel<<<dim3((ldw + 63) / 64, (nlist + 63) / 64), 256, 0, st>>>(nlist, list, D, N, ldw, X,
+                                                                           s0, s, W);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = ensure_dyn_smem(hess_logreg_tc_kernel, kSmemBytes);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -347,8 +382,8 @@ cudaError_t launch_hess_logreg_tc(int nlist, const int *list, int D, int N, cons
     const int npairs = (nlist + 1) / 2;
     const int grid = npairs < sms ? npairs : sms;
     hess_logreg_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(
-        nlist, list, D, N, static_cast<const unsigned char *>(img), s0, s, eps, inv_sp2, Jbuf,
-        timeout, spin_limit ? spin_limit : kDefaultSpinLimit);
+        nlist, D, N, static_cast<const unsigned char *>(img), W, ldw, eps, inv_sp2, Jbuf, timeout,
+        spin_limit ? spin_limit : kDefaultSpinLimit);
     return cudaGetLastError();
 }
 
