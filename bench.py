@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--workload", default="c2",
                     choices=["c2", "c1", "c3_diag", "c3_bf16", "c3_block", "c4", "c5",
-                             "gibbs_diag", "gibbs_dense",
+                             "gibbs_diag", "gibbs_dense", "adjoint_small",
                              "scan_sweep"],
                     help="c2 (default) is the headline line; the others measure the other "
                          "configurations")
@@ -501,6 +501,27 @@ def run_other(args):
                     newton_iters=res["iters"], status=res["status"], dtype="f32",
                     max_rel_dev_from_sequential=dev_max,
                     seq_gpu={"value": c.T / (sms / 1e3), "ms": sms, "speedup": sms / ms})
+    elif wl == "adjoint_small":
+        # the adjoint workload's shapes (N=5000, D=100) on a 600-step chain: a case small enough
+        # for a profiler capture of the tensor-core Jacobian kernel
+        c = W.C4
+        T = 600
+        X, y, _ = W.blr_data(c.N, c.D, seed=0, dtype=np.float32)
+        xi, u = W.noise(T, c.D, seed=0, dtype=np.float32)
+        tgt = P.Target("logreg", c.D, X=torch.tensor(X, device=dev), y=torch.tensor(y, device=dev))
+        s0 = torch.zeros(c.D, dtype=torch.float32, device=dev)
+        xid, ud = torch.tensor(xi, device=dev), torch.tensor(u, device=dev)
+        sopt = P.Options(sampler="mala", step=c.step, precision="f32")
+        s, _ = P.pmcmc_seq_solve(tgt, sopt, T, s0, xid, ud)
+        _, _, acc, _ = P.pmcmc_linearize(tgt, P.Options(sampler="mala", step=c.step, jac="zero",
+                                                        precision="f32"), T, s0, s, xid, ud,
+                                         want_jac=False)
+        dL = (2.0 * s / T).contiguous()
+        ams, g = _timed(lambda: P.pmcmc_adjoint(tgt, sopt, T, s0, s, acc, xid, ud, dL),
+                        args.steps, args.warmup, flush, stream, torch)
+        line.update(config=f"mala_logreg_n{c.N}_d{c.D}_t{T} adjoint", value=T / (ams / 1e3),
+                    ms_per_step=ams, adjoint={"ms": ams, "grad": g, "accepted": int(acc.sum().item())},
+                    dtype="f32")
     elif wl == "c4":
         c = W.C4
         X, y, _ = W.blr_data(c.N, c.D, seed=0, dtype=np.float32)

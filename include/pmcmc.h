@@ -129,6 +129,10 @@ typedef struct {
                              Jacobians on LOGREG, F32, 64 < D <= 128); 1: CUDA cores only */
     int seq_after;        /* pmcmc_solve_batched: 0 = off; > 0 = a chain not converged after
                              this many Newton sweeps is completed by the sequential loop */
+    int window;           /* pmcmc_solve: 0 = off; W > 0 = sliding-window updates (Section 3.4):
+                             each Newton iteration evaluates and updates only the W steps from
+                             the first step not yet converged, so the Jacobian and residual
+                             buffers hold W (not T) steps.  Not with Q or HMC_PAR_LEAPFROG. */
 } pmcmc_options;
 
 typedef struct {

@@ -122,6 +122,7 @@ class Options:
     spin_limit: int = 0
     engine: str = "auto"   # "auto": tensor cores where a kernel exists; "simt": CUDA cores only
     seq_after: int = 0     # batched: complete chains unconverged after this many sweeps sequentially
+    window: int = 0        # sliding-window Newton updates of this many steps (0: whole chain)
 
     def c(self) -> L.pmcmc_options:
         return L.pmcmc_options(SAMPLERS[self.sampler], float(self.step), int(self.leapfrog_L),
@@ -129,7 +130,7 @@ class Options:
                                float(self.rtol), int(self.max_iters), float(self.damping),
                                int(self.clip), int(self.gate_grad), int(self.seed),
                                int(self.chain_id), int(self.spin_limit),
-                               ENGINES[self.engine], int(self.seq_after))
+                               ENGINES[self.engine], int(self.seq_after), int(self.window))
 
 
 def _result_dict(r: L.pmcmc_result) -> dict:

@@ -32,7 +32,7 @@ class pmcmc_options(C.Structure):
                 ("rtol", C.c_double), ("max_iters", C.c_int), ("damping", C.c_double),
                 ("clip", C.c_int), ("gate_grad", C.c_int), ("seed", C.c_ulonglong),
                 ("chain_id", C.c_uint), ("spin_limit", C.c_int),
-                ("engine", C.c_int), ("seq_after", C.c_int)]
+                ("engine", C.c_int), ("seq_after", C.c_int), ("window", C.c_int)]
 
 
 class pmcmc_result(C.Structure):

@@ -165,6 +165,7 @@ void pmcmc_options_default(pmcmc_options *o) {
     o->spin_limit = 0;
     o->engine = 0;
     o->seq_after = 0;
+    o->window = 0;
 }
 
 pmcmc_status pmcmc_create(pmcmc_ctx **out, int device) {
@@ -475,6 +476,11 @@ extern "C" pmcmc_status pmcmc_solve(pmcmc_ctx *c, const pmcmc_target *tg,
     }
     PM_CUDA(c, cudaSetDevice(c->device));
     if (tg->Q) return solve_with_basis(c, tg, o, T, s0, s_init, xi, u, s_out, res, stream);
+    if (o->window > 0 && o->window < T) {
+        if (tg->Q || o->sampler == PMCMC_HMC_PAR_LEAPFROG)
+            return fail(c, PMCMC_EUNSUPPORTED, "sliding window: not with Q or HMC_PAR_LEAPFROG");
+        return window_solve(c, tg, o, T, s0, s_init, xi, u, s_out, res, stream);
+    }
     if (o->sampler == PMCMC_HMC_PAR_LEAPFROG)
         return solve_par_leapfrog(c, tg, o, T, s0, xi, u, s_out, res, stream);
     return newton_solve(c, tg, o, T, s0, s_init, xi, u, s_out, res, stream);
@@ -789,6 +795,199 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         res->max_residual = ord_decode(h->stats[0].rmax);
         res->accept_rate = (double)h->stats[0].accepts / (double)T;
         res->min_margin = ord_decode(h->stats[0].min_margin);
+        res->nonfinite_resets = (int)c->resets_accum;
+        res->elapsed_ms = ms;
+    }
+    c->resets_accum = 0;
+    return status;
+}
+
+// ------------------------------------------------------------------------------------------
+// Sliding-window Newton updates (Section 3.4): each iteration evaluates f_t and J_t on the W
+// steps from t0, the first step whose residual is not yet within tolerance, moves t0 past the
+// converged prefix of the window, and applies the Newton update to the rest of the window with
+// the carry zero at the new t0 (its predecessor is converged and is never changed again).  The
+// first step after t0 is exact after one update, so t0 advances every iteration.
+// ------------------------------------------------------------------------------------------
+template <typename R, typename S_>
+__global__ void first_unconverged_kernel(int n, int D, const S_ *__restrict__ r,
+                                         const R *__restrict__ s, double atol, double rtol,
+                                         int *first) {
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (e >= (size_t)n * D) return;
+    const double rv = fabs((double)load_as<S_, R>(r + e)), sv = fabs((double)s[e]);
+    const double v = rv - rtol * sv;
+    if (!(v <= atol)) atomicMin(first, (int)(e / D));  // NaN counts as not converged
+}
+
+// accepted steps among the window's first *first steps (the prefix that becomes frozen)
+__global__ void window_accepts_kernel(const unsigned char *acc, const int *first, int *count) {
+    int local = 0;
+    const int k = *first;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k; t += gridDim.x * blockDim.x) local += acc[t];
+    local = warp_sum(local);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+__global__ void set_int_kernel(int *p, int v) { *p = v; }
+
+pmcmc_status window_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
+                          const void *s0, const void *s_init, const void *xi, const double *u,
+                          void *s_out, pmcmc_result *res, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = tg->D;
+    const bool f64 = o->precision == PMCMC_F64;
+    const bool bf16 = o->precision == PMCMC_F32_SCAN_BF16;
+    const int rb = f64 ? 8 : 4;
+    const int W = o->window;
+    const bool gen = xi == nullptr;
+    Plan p = make_plan(tg, o, W, false, false);
+    Carve cv;
+    cv.used = p.bytes;
+    const size_t o_xi = gen ? cv.take((size_t)rb * T * D) : 0;
+    const size_t o_u = gen ? cv.take(sizeof(double) * (size_t)T) : 0;
+    pmcmc_status ps = ws_reserve(c, cv.used);
+    if (ps != PMCMC_OK) return ps;
+    char *base = (char *)c->ws;
+    ScanWork w;
+    w.flags = (unsigned int *)(base + p.o_flags);
+    w.agg = base + p.o_agg;
+    w.incl = base + p.o_incl;
+    w.max_tiles = p.tiles;
+    w.ctl = &c->ctl->scan;
+    PM_CUDA(c, cudaMemsetAsync(w.flags, 0, sizeof(unsigned int) * p.tiles, st));
+    c->flags_generation = ~0ull;  // the next whole-chain solve re-zeroes its flag area
+    if (gen) {
+        xi = base + o_xi;
+        u = (const double *)(base + o_u);
+        PM_CUDA(c, launch_noise(o->seed, o->chain_id, T, D, f64, (void *)xi, (double *)u, st));
+    }
+    if (tg->kind == PMCMC_LOGREG) {
+        const int DP = logreg_padded_dim(D);
+        const int Npad = ceil_div(tg->N, 64) * 64;
+        pad_rows_kernel<<<grid_for((size_t)Npad * DP), 256, 0, st>>>(base + p.o_xp, tg->X, tg->N,
+                                                                     D, Npad, DP, rb);
+        PM_CUDA(c, cudaGetLastError());
+        if (p.tc) PM_CUDA(c, launch_logreg_tc_pack(tg->X, tg->y, tg->N, D, base + p.o_img, st));
+    }
+    if (s_init) {
+        if (s_init != s_out)
+            PM_CUDA(c, cudaMemcpyAsync(s_out, s_init, (size_t)rb * T * D, cudaMemcpyDeviceToDevice, st));
+    } else {
+        broadcast_rows_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(s_out, s0, T, D, rb);
+        PM_CUDA(c, cudaGetLastError());
+    }
+    {
+        int *flag = &c->ctl->nonfinite_input;
+        PM_CUDA(c, cudaMemsetAsync(flag, 0, sizeof(int), st));
+        finite_check_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(s_out, (size_t)T * D, rb, flag);
+        finite_check_kernel<<<1, 256, 0, st>>>(s0, (size_t)D, rb, flag);
+        PM_CUDA(c, cudaGetLastError());
+    }
+    EvalArgs A;
+    fill_eval_args(A, tg, o, W);
+    A.Xp = base + p.o_xp;
+    A.a_out = base + p.o_a;
+    A.b_out = base + p.o_b;
+    A.acc_out = (unsigned char *)(base + p.o_acc);
+    if (tg->kind == PMCMC_LOGREG && o->jac == PMCMC_JAC_DENSE) {
+        A.w_out = base + p.o_w;
+        A.rank1_u = base + p.o_ru;
+        A.rank1_v = base + p.o_rv;
+    }
+    EvalStats *stats = &c->ctl->stats[0];
+    A.stats = stats;
+    A.iter = &c->ctl->iter;
+    const unsigned int spin = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
+    if (p.tc) A.tc_img = base + p.o_img;
+    A.timeout = &c->ctl->scan.timeout;
+    A.spin_limit = spin;
+    const int max_iters = o->max_iters > 0 ? o->max_iters : T;
+    const size_t jrow = o->jac == PMCMC_JAC_DENSE ? (size_t)D * D : (size_t)D;
+    const int sb = bf16 ? 2 : rb;
+    CtlBlock *h = c->host_ctl;
+    int *first = &c->ctl->first_bad, *wacc = &c->ctl->win_accepts;
+    PM_CUDA(c, cudaMemsetAsync(wacc, 0, sizeof(int), st));
+    PM_CUDA(c, cudaEventRecord(c->ev0, st));
+    int it = 0, t0 = 0;
+    bool converged = false;
+    double rmax = 0.0, margin = INFINITY;
+    for (;;) {
+        const int n = std::min(W, T - t0);
+        A.T = n;
+        A.s0 = t0 == 0 ? s0 : (const char *)s_out + (size_t)rb * (t0 - 1) * D;
+        A.s = (char *)s_out + (size_t)rb * t0 * D;
+        A.xi = (const char *)xi + (size_t)rb * t0 * D;
+        A.u = u + t0;
+        PM_CUDA(c, cudaMemcpyAsync(&c->ctl->iter, &it, sizeof(int), cudaMemcpyHostToDevice, st));
+        stats_reset_kernel<<<1, 32, 0, st>>>(stats, 1);
+        if (tg->kind == PMCMC_LOGREG) {
+            PM_CUDA(c, launch_eval_logreg(A, st));
+            if (o->jac == PMCMC_JAC_DENSE) PM_CUDA(c, launch_logreg_dense_jac(A, st));
+        } else {
+            PM_CUDA(c, launch_eval_small(A, st));
+        }
+        set_int_kernel<<<1, 1, 0, st>>>(first, n);
+        const size_t ne = (size_t)n * D;
+        if (f64)
+            first_unconverged_kernel<double, double><<<grid_for(ne), 256, 0, st>>>(
+                n, D, (const double *)A.b_out, (const double *)A.s, o->atol, o->rtol, first);
+        else if (bf16)
+            first_unconverged_kernel<float, __nv_bfloat16><<<grid_for(ne), 256, 0, st>>>(
+                n, D, (const __nv_bfloat16 *)A.b_out, (const float *)A.s, o->atol, o->rtol, first);
+        else
+            first_unconverged_kernel<float, float><<<grid_for(ne), 256, 0, st>>>(
+                n, D, (const float *)A.b_out, (const float *)A.s, o->atol, o->rtol, first);
+        window_accepts_kernel<<<std::max(1, std::min(64, ceil_div(n, 256))), 256, 0, st>>>(A.acc_out, first, wacc);
+        PM_CUDA(c, cudaGetLastError());
+        PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(c, cudaStreamSynchronize(st));
+        if (h->nonfinite_input) return fail(c, PMCMC_ENAN, "s0 or the initial guess is not finite");
+        rmax = std::max(rmax, ord_decode(h->stats[0].rmax));
+        margin = std::min(margin, ord_decode(h->stats[0].min_margin));
+        const int k = h->first_bad;
+        if (t0 + k >= T) {
+            converged = true;
+            break;
+        }
+        if (k == n) {  // the whole window is converged: move on without an update
+            t0 += k;
+            continue;
+        }
+        if (it >= max_iters) break;
+        // update the unconverged rest of the window, [t0 + k, t0 + n), with the carry zero at t0 + k
+        const void *a = (const char *)A.a_out + (size_t)(o->jac == PMCMC_JAC_DENSE ? rb : sb) * k * jrow;
+        const void *b = (const char *)A.b_out + (size_t)sb * k * D;
+        void *sw = (char *)s_out + (size_t)rb * (t0 + k) * D;
+        if (o->jac == PMCMC_JAC_DENSE)
+            PM_CUDA(c, launch_scan_dense(f64, n - k, D, p.tile_t, a, b, sw, s0, w, stats, nullptr, spin, st));
+        else
+            PM_CUDA(c, launch_scan_diag(f64, bf16 ? 1 : 0, n - k, D, p.tile_t, a, b, sw, s0, w, stats,
+                                        nullptr, spin, st));
+        it++;
+        t0 += k;
+        PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(c, cudaStreamSynchronize(st));
+        c->resets_accum += h->stats[0].resets;
+        if (h->scan.timeout) break;
+    }
+    PM_CUDA(c, cudaEventRecord(c->ev1, st));
+    PM_CUDA(c, cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    pmcmc_status status = converged ? PMCMC_OK : PMCMC_NOT_CONVERGED;
+    if (h->scan.timeout) {
+        unsigned int zero = 0;
+        cudaMemcpy(&c->ctl->scan.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        status = PMCMC_ETIMEOUT;
+        fail(c, status, "a bounded wait (scan look-back or evaluate pipeline) ran out");
+    }
+    if (res) {
+        res->iters = it;
+        res->status = status;
+        res->max_residual = rmax;
+        res->accept_rate = (double)h->win_accepts / (double)T;
+        res->min_margin = margin;
         res->nonfinite_resets = (int)c->resets_accum;
         res->elapsed_ms = ms;
     }

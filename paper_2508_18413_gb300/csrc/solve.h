@@ -24,7 +24,9 @@ struct CtlBlock {
     int converged;
     int skip;             // device-side loop: set once the loop is finished
     int iters_done;
-    int pad[3];
+    int first_bad;        // sliding window: first step of the window not yet converged
+    int win_accepts;      // sliding window: accepted steps of the frozen prefix
+    int pad;
     unsigned long long inner_iters;  // parallel leapfrog: inner Newton iterations, all steps
     unsigned long long inner_max;
 };
@@ -75,6 +77,9 @@ pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opt
                            const void *s0, bool sequential);
 void fill_eval_args(EvalArgs &A, const pmcmc_target *tg, const pmcmc_options *o, int T);
 pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
+                          const void *s0, const void *s_init, const void *xi, const double *u,
+                          void *s_out, pmcmc_result *res, void *stream);
+pmcmc_status window_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
                           const void *s0, const void *s_init, const void *xi, const double *u,
                           void *s_out, pmcmc_result *res, void *stream);
 pmcmc_status solve_par_leapfrog(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o,
