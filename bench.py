@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--c5-seq-after", type=int, default=150,
                     help="c5: Newton sweeps after which an unconverged chain is completed by the "
                          "sequential loop (0: Newton only)")
-    ap.add_argument("--scan-kernel", choices=["rows", "staged", "pipe"], default=None,
+    ap.add_argument("--scan-kernel", choices=["rows", "staged", "pipe", "pipe2"], default=None,
                     help="diagonal scan kernel for D <= 32 (default: the library's choice)")
     return ap.parse_args()
 
@@ -657,7 +657,8 @@ def _measured_hbm():
 def main():
     args = parse()
     if args.scan_kernel:
-        os.environ["PMCMC_SCAN_KERNEL"] = args.scan_kernel
+        os.environ["PMCMC_SCAN_KERNEL"] = "pipe" if args.scan_kernel == "pipe2" else args.scan_kernel
+        os.environ["PMCMC_PIPE_CTAS"] = "2" if args.scan_kernel == "pipe2" else "1"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "c2":

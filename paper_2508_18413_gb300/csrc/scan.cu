@@ -1023,15 +1023,25 @@ static size_t staged_smem(int TT, int D, int rbytes, int sbytes) {
     return 2 * ((E * sbytes + 15) & ~(size_t)15) + E * rbytes;
 }
 
+// CTAs per SM of the pipelined kernel: PMCMC_PIPE_CTAS = 1 or 2 (read at every launch; default
+// 1).  With two, each CTA holds half the shared memory (smaller tiles) and one CTA's barrier
+// and look-back latency overlaps the other's work.
+static int pipe_ctas() {
+    const char *e = getenv("PMCMC_PIPE_CTAS");
+    return (e && e[0] == '2') ? 2 : 1;
+}
+
 // Run length M of the pipelined kernel (its tile is 8 P M timesteps): two tile buffers of a, b
-// and s within about 216 KB of shared memory, at least two tiles per SM where T allows, and
-// M - 1 a multiple of 32 / gcd(D, 32) (the P runs of a warp then start in distinct banks) unless
-// that would halve the run.
-static int pipe_run(int T, int D, int sbytes, int rbytes) {
+// and s within about 216 KB of shared memory per SM (200 KB with two CTAs, each also holding its
+// static shared memory), at least two tiles per CTA where T allows,
+// and M - 1 a multiple of 32 / gcd(D, 32) (the P runs of a warp then start in distinct banks)
+// unless that would halve the run.
+static int pipe_run(int T, int D, int sbytes, int rbytes, int ctas) {
     const int P = 32 / D;
     const int per_elem = 2 * sbytes + rbytes;
-    const int m_max = std::max(1, (108 * 1024) / (8 * P * D * per_elem));
-    const int spread = std::max(1, ceil_div(T, 2 * 152 * 8 * P));
+    const int buf = ctas == 1 ? 108 * 1024 : 50 * 1024;  // two buffers (+ static) per CTA
+    const int m_max = std::max(1, buf / (8 * P * D * per_elem));
+    const int spread = std::max(1, ceil_div(T, 2 * 152 * ctas * 8 * P));
     const int cap = std::min(m_max, spread);
     if (P == 1) return cap;
     const int c = 32 / std::gcd(D, 32);
@@ -1061,7 +1071,7 @@ static int scan_kernel_choice(long long elems) {
 int diag_scan_tile(int T, int D, int elem_bytes) {
     if (D <= 32)  // the smallest tile of the kernels that may run sizes the workspace
         return std::min({diag_scan_tile_rows(T, D), staged_tile(T, D, elem_bytes),
-                         8 * (32 / D) * pipe_run(T, D, elem_bytes, elem_bytes)});
+                         8 * (32 / D) * pipe_run(T, D, elem_bytes, elem_bytes, 2)});
     // enough tiles to fill the GPU twice over, at most ~4096 elements (FP32) per tile
     const int max_elems = elem_bytes >= 8 ? 2048 : 4096;
     int tt_max = std::max(8, (max_elems / std::max(D, 1)) / 8 * 8);
@@ -1228,7 +1238,7 @@ template <typename R, typename S>
 static cudaError_t run_scan_pipe(int T, int D, const void *a, const void *b, void *s,
                                  const void *s_reset, const ScanWork &w, EvalStats *stats,
                                  const int *skip, unsigned int spin, cudaStream_t st) {
-    const int M = pipe_run(T, D, sizeof(S), sizeof(R));
+    const int M = pipe_run(T, D, sizeof(S), sizeof(R), pipe_ctas());
     const int ntiles = ceil_div(T, 8 * (32 / D) * M);
     if (ntiles > w.max_tiles) return cudaErrorInvalidValue;
     const size_t sm = pipe_smem(M, D, sizeof(S), sizeof(R));

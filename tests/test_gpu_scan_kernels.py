@@ -19,18 +19,21 @@ if torch.cuda.is_available():
     import paper_2508_18413_gb300 as P
 
 DEV = "cuda:0"
-KERNELS = ["rows", "staged", "pipe"]
+KERNELS = ["rows", "staged", "pipe", "pipe2"]
 
 
 @pytest.fixture
 def kernel(request):
-    old = os.environ.get("PMCMC_SCAN_KERNEL")
-    os.environ["PMCMC_SCAN_KERNEL"] = request.param
+    """rows, staged, pipe (one CTA per SM) or pipe2 (two CTAs per SM, smaller tiles)."""
+    saved = {k: os.environ.get(k) for k in ("PMCMC_SCAN_KERNEL", "PMCMC_PIPE_CTAS")}
+    os.environ["PMCMC_SCAN_KERNEL"] = "pipe" if request.param == "pipe2" else request.param
+    os.environ["PMCMC_PIPE_CTAS"] = "2" if request.param == "pipe2" else "1"
     yield request.param
-    if old is None:
-        del os.environ["PMCMC_SCAN_KERNEL"]
-    else:
-        os.environ["PMCMC_SCAN_KERNEL"] = old
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
 
 
 def _run(precision, a, b, s):
