@@ -62,7 +62,7 @@ typedef enum {
  *   GAUSSIAN: -1/2 (x - mean)^T prec (x - mean)
  *   LOGREG:   sum_n [y_n z_n - log(1 + exp z_n)] - |x|^2 / (2 prior_scale^2),  z = X x
  *   BANANA:   -x1^2/200 - (x2 + 0.1 x1^2 - 10)^2 / 2   (D = 2)
- *   SCHOOLS:  the hierarchical Gaussian model of the Gibbs experiment (Appendix B.1): S schools
+ *   SCHOOLS:  the hierarchical Gaussian model of the Gibbs experiment (Appendix B.2): S schools
  *             of N scores (X: S x N, row s = school s), state (tau^2, mu, theta_1..S,
  *             sigma^2_1..S), D = 2 + 2S, 1 <= S <= 15, hyperparameters nu0 = 0.1,
  *             tau0^2 = 100, mu0 = 0, kappa0 = 0.1, alpha0 = 0.1, sigma0^2 = 10.  Sampled by

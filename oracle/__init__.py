@@ -75,7 +75,7 @@ def _ptr(a, typ=_dp):
 @dataclass
 class Target:
     """A target density: 'gaussian' (mu, P = precision), 'logreg' (X, y, sigma_p), 'banana',
-    or 'schools' (the hierarchical Gaussian model of the Gibbs experiment, Appendix B.1: X holds
+    or 'schools' (the hierarchical Gaussian model of the Gibbs experiment, Appendix B.2: X holds
     the scores, S schools x N students, and D = 2 + 2 S)."""
     kind: str
     D: int
@@ -180,7 +180,7 @@ def leapfrog(t: Target, eps, s):
 
 
 def gibbs_sweep(t: Target, s_prev, xi):
-    """One reparameterised Gibbs sweep of the schools model (Section 3.1, Appendix B.1).
+    """One reparameterised Gibbs sweep of the schools model (Section 3.1, Appendix B.2).
     Returns (next state, its Jacobian d next / d s_prev)."""
     s_prev, xi = _arr(s_prev), _arr(xi)
     out = np.zeros(t.D)

@@ -10,7 +10,7 @@
  *   - transitions f_t: MALA (Section 3.2), HMC with a sequential leapfrog (Algorithm 2), one
  *     leapfrog step on [x, v] (Eq. 7), MALA without the MH correction (ULA, for the affine
  *     special case of Section 2), and the reparameterised Gibbs sweep of the hierarchical
- *     Gaussian model (Section 3.1, Appendix B.1);
+ *     Gaussian model (Section 3.1, Appendix B.2);
  *   - the sequential chain s_t = f_t(s_{t-1}) (Section 2), which is the exact answer;
  *   - the Newton Jacobians: the stop-gradient relaxation of the accept/reject gate
  *     (Section 3.2), its diagonal (quasi-DEER, Eq. 4), the leapfrog Jacobian (Eq. 8) and its
@@ -286,7 +286,7 @@ void o_leapfrog(const o_target *tg, double eps, const double *s, double *out) {
 /*
  * Reparameterised Gibbs sweep of the hierarchical Gaussian ("eight schools") model of the Gibbs
  * experiment (Section 3.1, Eq. 5-6; the model, its hyperparameters and the coordinate order are
- * those of Appendix B.1).  S schools with N scores each, X[s*N + n]; state
+ * those of Appendix B.2).  S schools with N scores each, X[s*N + n]; state
  *   s = (tau^2, mu, theta_1..theta_S, sigma^2_1..sigma^2_S),  D = 2 + 2S.
  * Model: tau^2 ~ Inv-chi^2(nu0, tau0^2), mu | tau^2 ~ N(mu0, tau^2 / kappa0),
  * theta_s | mu, tau^2 ~ N(mu, tau^2), sigma^2_s ~ Inv-chi^2(alpha0, sigma0^2),
@@ -302,7 +302,7 @@ void o_leapfrog(const o_target *tg, double eps, const double *s, double *out) {
  * tau^2 and mu use the previous sweep's theta and mu, theta_s the previous sigma^2_s, so the sweep
  * does not depend on the previous tau^2 (Eq. 6).  Reparameterisation: the noise xi (D values) holds
  * xi[0] ~ Inv-chi^2(nu0 + S + 1, 1), xi[1] and xi[2 + s] ~ N(0, 1), xi[2 + S + s] ~
- * Inv-chi^2(alpha0 + N, 1); an Inv-chi^2(nu, 1) variate times c is Inv-chi^2(nu, c) (Appendix B.1),
+ * Inv-chi^2(alpha0 + N, 1); an Inv-chi^2(nu, 1) variate times c is Inv-chi^2(nu, c) (Appendix B.2),
  * a standard normal times sd plus mean is N(mean, sd^2).
  * J (may be NULL): the D x D Jacobian d out / d s_prev, row by row in the order of the updates
  * (forward-mode chain rule through the sweep).

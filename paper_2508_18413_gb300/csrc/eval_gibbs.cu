@@ -4,7 +4,7 @@
 // Section 3.1 writes a Gibbs sweep as a deterministic, differentiable function of the previous
 // state and per-sweep noise, x_t = f(x_{t-1}, xi_t) (Eq. 5), composed of one update per
 // coordinate, each conditioned on the newest values of the others (Eq. 6).  The model and the
-// order of its updates are those of the Gibbs experiment (Appendix B.1): S schools of N scores,
+// order of its updates are those of the Gibbs experiment (Appendix B.2): S schools of N scores,
 //   tau^2 ~ Inv-chi^2(nu0, tau0^2),  mu | tau^2 ~ N(mu0, tau^2 / kappa0),
 //   theta_s | mu, tau^2 ~ N(mu, tau^2),  sigma^2_s ~ Inv-chi^2(alpha0, sigma0^2),
 //   x_sn ~ N(theta_s, sigma^2_s),

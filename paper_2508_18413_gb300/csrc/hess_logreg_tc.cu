@@ -3,7 +3,7 @@
 // For the adjoint (the reverse recursion of the fixed point with the decisions held), every
 // accepted step t needs J_t = I + eps H(x_t) with x_t = s_{t-1} and
 //   H(x) = -X^T diag(w) X - I / sigma_p^2,   w_n = sigmoid(z_n) (1 - sigmoid(z_n)),   z = X x,
-// an N x D x D contraction per step: the dominant work of the adjoint (Section 3.4's MALA
+// an N x D x D contraction per step: the dominant work of the adjoint (Section 3.2's MALA
 // Jacobian with the gate held; the reverse recursion itself is D^3 per step).  This file forms
 // it for 64 < D <= 128 as a tcgen05 product with FP32 accuracy:
 //

@@ -1,5 +1,5 @@
 """Reparameterised Gibbs on the hierarchical Gaussian (schools) model: the CUDA path against the
-FP64 oracle (Section 3.1, Appendix B.1).
+FP64 oracle (Section 3.1, Appendix B.2).
 
 Bars: FP64 1e-9 relative to the oracle (f, J, the Newton fixed point, the sequential chain);
 FP32 f within 1e-5 (1 + |f|), J within 1e-4 (1 + |J|), traces within 1e-5 (1 + |s|)."""

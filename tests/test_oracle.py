@@ -540,10 +540,10 @@ def test_linear_recursion_is_sum_of_products(dense):
 
 
 # ------------------------------------------------------------------------------------------
-# Reparameterised Gibbs on the hierarchical Gaussian (schools) model (Section 3.1, App. B.1)
+# Reparameterised Gibbs on the hierarchical Gaussian (schools) model (Section 3.1, App. B.2)
 # ------------------------------------------------------------------------------------------
 
-# hyperparameters stated in Appendix B.1
+# hyperparameters stated in Appendix B.2
 _NU0, _TAU0SQ, _MU0, _KAPPA0, _ALPHA0, _SIGMA0SQ = 0.1, 100.0, 0.0, 0.1, 0.1, 10.0
 
 

@@ -15,7 +15,7 @@ Input recipe (all seeds default to 0; draws are taken in the order listed):
 * Sampler noise (Section 3.2 / Algorithm 2): ``xi_t ~ N(0, I_D)`` per step and
   ``u_t ~ U(0, 1)`` on the open interval, ``u = (k + 0.5) 2^-53`` with ``k`` a uniform 53-bit
   integer, so ``log u`` is always finite.
-* Hierarchical Gaussian ("eight schools") Gibbs workload (Section 5.1, Appendix B.1): S = 8
+* Hierarchical Gaussian ("eight schools") Gibbs workload (Section 5.1, Appendix B.2): S = 8
   schools of N = 20 scores.  The paper matched its synthetic scores to a published table of
   school means and standard errors; that table is not reproduced here.  Instead school means
   ~ N(5, 10^2), school standard deviations ~ U(5, 20), scores = mean + sd * N(0, 1).  The Gibbs
@@ -83,7 +83,7 @@ def noise(T: int, D: int, seed: int = 0, dtype=np.float64):
     return xi.astype(dtype), u
 
 
-# degrees of freedom of the two scaled-inverse-chi-square priors of the schools model (App. B.1)
+# degrees of freedom of the two scaled-inverse-chi-square priors of the schools model (App. B.2)
 SCHOOLS_NU0 = 0.1
 SCHOOLS_ALPHA0 = 0.1
 
