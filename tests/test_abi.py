@@ -58,3 +58,35 @@ int main(void){printf("%zu %zu %zu %zu\n", sizeof(pmcmc_target), sizeof(pmcmc_op
         sizes = list(map(int, subprocess.check_output([exe]).split()))
     assert sizes == [C.sizeof(_lib.pmcmc_target), C.sizeof(_lib.pmcmc_options),
                      C.sizeof(_lib.pmcmc_result), C.sizeof(_lib.pmcmc_chain_desc)]
+
+
+def test_struct_field_offsets_match_header():
+    """Every field of the Python mirrors sits at the C offset (offsetof in a compiled probe), so
+    a field added on one side only cannot shift the others unnoticed."""
+    from paper_2508_18413_gb300 import _lib
+    import subprocess, tempfile
+    structs = [("pmcmc_target", _lib.pmcmc_target), ("pmcmc_options", _lib.pmcmc_options),
+               ("pmcmc_result", _lib.pmcmc_result), ("pmcmc_chain_desc", _lib.pmcmc_chain_desc)]
+    lines = []
+    for cname, py in structs:
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    prog = ("#include <stdio.h>\n#include <stddef.h>\n#include \"pmcmc.h\"\nint main(void){\n" +
+            "\n".join(lines) + "\nreturn 0;}\n")
+    with tempfile.TemporaryDirectory() as d:
+        cfile = os.path.join(d, "p.c")
+        open(cfile, "w").write(prog)
+        exe = os.path.join(d, "p")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), cfile, "-o", exe])
+        got = dict(l.split() for l in subprocess.check_output([exe]).decode().splitlines())
+    for cname, py in structs:
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_options_default_leaves_extensions_off():
+    from paper_2508_18413_gb300 import _lib
+    lib = _lib.load()
+    o = _lib.pmcmc_options()
+    lib.pmcmc_options_default(C.byref(o))
+    assert o.window == 0 and o.seq_after == 0 and o.engine == 0 and o.sampler == 0
