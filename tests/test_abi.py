@@ -90,3 +90,31 @@ def test_options_default_leaves_extensions_off():
     o = _lib.pmcmc_options()
     lib.pmcmc_options_default(C.byref(o))
     assert o.window == 0 and o.seq_after == 0 and o.engine == 0 and o.sampler == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """The binding has no CPU path: without the built library it raises instead of computing."""
+    import subprocess
+    import sys
+    code = ("import paper_2508_18413_gb300._lib as L\n"
+            "L._lib = None\n"
+            f"L.load({str(tmp_path / 'absent.so')!r})\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode != 0 and "no fallback" in r.stderr.replace("\n", " ")
+
+
+def test_reference_arm_json_contract():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) prints one JSON line with
+    the contract's keys and runs without a GPU."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
