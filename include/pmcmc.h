@@ -194,6 +194,20 @@ pmcmc_status pmcmc_solve(pmcmc_ctx *ctx, const pmcmc_target *target, const pmcmc
  * Section 5: one dependent step after another).  Same arguments as pmcmc_solve without the
  * Newton controls.  accept_out (T bytes, device, may be NULL) receives the decisions.
  */
+/*
+ * pmcmc_solve without a host synchronisation: the whole Newton loop is enqueued on `stream` (the
+ * device-side loop of a conditional CUDA graph) followed by a kernel that writes the result to
+ * res_dev, a pmcmc_result in DEVICE memory; the call returns once the work is enqueued.  The
+ * solve's outcome (PMCMC_OK, PMCMC_NOT_CONVERGED, PMCMC_ENAN, PMCMC_ETIMEOUT) is in
+ * res_dev->status; the return value reports argument and launch errors only (PMCMC_EUNSUPPORTED
+ * with Q, PMCMC_HMC_PAR_LEAPFROG, a window, profiling on, or where conditional graphs are not
+ * available).  res_dev->elapsed_ms is 0.  s_out, xi, u and res_dev must stay valid, and the
+ * context unused by other calls, until the stream has passed this call.
+ */
+pmcmc_status pmcmc_solve_async(pmcmc_ctx *ctx, const pmcmc_target *target, const pmcmc_options *opt,
+                               int T, const void *s0, const void *s_init, const void *xi,
+                               const double *u, void *s_out, pmcmc_result *res_dev, void *stream);
+
 pmcmc_status pmcmc_seq_solve(pmcmc_ctx *ctx, const pmcmc_target *target,
                              const pmcmc_options *opt, int T, const void *s0, const void *xi,
                              const double *u, void *s_out, unsigned char *accept_out,

@@ -18,6 +18,7 @@ from ._lib import ENGINES, JACS, PRECISIONS, SAMPLERS, STATUS_NAMES, TARGETS
 __all__ = [
     "PmcmcError", "Target", "Options", "pmcmc_create", "pmcmc_gen_noise", "pmcmc_solve",
     "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan", "pmcmc_adjoint", "pmcmc_solve_batched",
+    "pmcmc_solve_async", "result_from_device",
     "ChainDesc", "real_dtype", "loaded_library_path", "pmcmc_profile_enable",
     "pmcmc_profile_get", "pmcmc_scan_noalloc", "ChainSolve", "solve_differentiable",
 ]
@@ -169,6 +170,35 @@ def pmcmc_solve(target: Target, opt: Options, T: int, s0: torch.Tensor, s_init=N
                               _ptr(u), _ptr(s_out), C.byref(res), _stream())
     _check(ctx, st)
     return s_out, _result_dict(res)
+
+
+def pmcmc_solve_async(target: Target, opt: Options, T: int, s0: torch.Tensor, s_init=None,
+                      xi=None, u=None, s_out=None):
+    """Enqueue the solve on the current stream without synchronising; returns (s [T, D],
+    res_dev), res_dev a device tensor holding the pmcmc_result, to be read with
+    result_from_device() once the stream has passed the solve.  The inputs are kept alive with
+    the returned handle."""
+    ctx = pmcmc_create()
+    dt = real_dtype(opt.precision)
+    s0 = _dev(s0, dt, "s0")
+    s_init = _dev(s_init, dt, "s_init")
+    xi = _dev(xi, dt, "xi")
+    u = _dev(u, torch.float64, "u")
+    if s_out is None:
+        s_out = torch.empty((T, target.D), dtype=dt, device="cuda")
+    res_dev = torch.zeros(C.sizeof(L.pmcmc_result), dtype=torch.uint8, device="cuda")
+    tc, oc = target.c(dt), opt.c()
+    st = L.load().pmcmc_solve_async(ctx, C.byref(tc), C.byref(oc), T, _ptr(s0), _ptr(s_init),
+                                    _ptr(xi), _ptr(u), _ptr(s_out), _ptr(res_dev), _stream())
+    _check(ctx, st)
+    res_dev._keep = (s0, s_init, xi, u, target)
+    return s_out, res_dev
+
+
+def result_from_device(res_dev: torch.Tensor) -> dict:
+    """The pmcmc_result written by pmcmc_solve_async (synchronises with the copy)."""
+    raw = bytes(res_dev.cpu().numpy().tobytes())
+    return _result_dict(L.pmcmc_result.from_buffer_copy(raw))
 
 
 def pmcmc_seq_solve(target: Target, opt: Options, T: int, s0, xi, u, s_out=None, accept=None):

@@ -87,6 +87,9 @@ def load(path: str = LIB_PATH):
     lib.pmcmc_solve.argtypes = [vp, C.POINTER(pmcmc_target), C.POINTER(pmcmc_options), i, vp,
                                 vp, vp, vp, vp, C.POINTER(pmcmc_result), vp]
     lib.pmcmc_solve.restype = st
+    lib.pmcmc_solve_async.argtypes = [vp, C.POINTER(pmcmc_target), C.POINTER(pmcmc_options), i,
+                                      vp, vp, vp, vp, vp, vp, vp]
+    lib.pmcmc_solve_async.restype = st
     lib.pmcmc_seq_solve.argtypes = [vp, C.POINTER(pmcmc_target), C.POINTER(pmcmc_options), i,
                                     vp, vp, vp, vp, vp, vp]
     lib.pmcmc_seq_solve.restype = st

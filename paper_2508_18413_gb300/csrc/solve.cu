@@ -486,6 +486,28 @@ extern "C" pmcmc_status pmcmc_solve(pmcmc_ctx *c, const pmcmc_target *tg,
     return newton_solve(c, tg, o, T, s0, s_init, xi, u, s_out, res, stream);
 }
 
+extern "C" pmcmc_status pmcmc_solve_async(pmcmc_ctx *c, const pmcmc_target *tg,
+                                          const pmcmc_options *o, int T, const void *s0,
+                                          const void *s_init, const void *xi, const double *u,
+                                          void *s_out, pmcmc_result *res_dev, void *stream) {
+    if (!c) return PMCMC_EINVAL;
+    pmcmc_status ps = check_problem(c, tg, o, T, s0, false);
+    if (ps != PMCMC_OK) return ps;
+    if (!res_dev) return fail(c, PMCMC_EINVAL, "res_dev is NULL");
+    if (T > 0 && !s_out) return fail(c, PMCMC_EINVAL, "s_out is NULL");
+    if ((xi == nullptr) != (u == nullptr)) return fail(c, PMCMC_EINVAL, "pass both xi and u, or neither");
+    if (o->sampler == PMCMC_GIBBS && !xi)
+        return fail(c, PMCMC_EINVAL, "Gibbs needs xi (its reparameterisation noise) and u");
+    if (tg->Q || o->sampler == PMCMC_HMC_PAR_LEAPFROG || (o->window > 0 && o->window < T))
+        return fail(c, PMCMC_EUNSUPPORTED, "async solve: not with Q, HMC_PAR_LEAPFROG or a window");
+    PM_CUDA(c, cudaSetDevice(c->device));
+    if (T == 0) {  // all-zero result: status PMCMC_OK, no iterations
+        PM_CUDA(c, cudaMemsetAsync(res_dev, 0, sizeof(pmcmc_result), (cudaStream_t)stream));
+        return PMCMC_OK;
+    }
+    return newton_solve(c, tg, o, T, s0, s_init, xi, u, s_out, nullptr, stream, res_dev);
+}
+
 namespace pm {
 
 // Device-side control of the Newton loop (Algorithm 1): decides convergence from the residual
@@ -598,9 +620,27 @@ static pmcmc_status build_loop_graph(pmcmc_ctx *c, const std::string &key, const
     return PMCMC_OK;
 }
 
+// The result of a device-side loop, written on the device (pmcmc_solve_async): the same fields
+// the synchronous path reads back from the control block.
+__global__ void write_result_kernel(CtlBlock *c, int T, pmcmc_result *r) {
+    const bool timeout = c->scan.timeout != 0;
+    r->status = c->nonfinite_input ? PMCMC_ENAN
+                : timeout          ? PMCMC_ETIMEOUT
+                : c->converged     ? PMCMC_OK
+                                   : PMCMC_NOT_CONVERGED;
+    if (timeout) c->scan.timeout = 0;
+    r->iters = c->iter;
+    r->max_residual = ord_decode(c->stats[1].rmax);
+    r->accept_rate = (double)c->stats[1].accepts / (double)T;
+    r->min_margin = ord_decode(c->stats[1].min_margin);
+    r->nonfinite_resets = (int)c->stats[0].resets;
+    r->elapsed_ms = 0.0f;
+    r->sequential = 0;
+}
+
 pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
                           const void *s0, const void *s_init, const void *xi, const double *u,
-                          void *s_out, pmcmc_result *res, void *stream) {
+                          void *s_out, pmcmc_result *res, void *stream, pmcmc_result *res_dev) {
     cudaStream_t st = (cudaStream_t)stream;
     const int D = tg->D;
     const bool f64 = o->precision == PMCMC_F64;
@@ -697,6 +737,14 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
                  o->gate_grad, o->atol, o->rtol, max_iters, spin, o->seed, o->chain_id, o->engine, s0, s_out,
                  xi, (const void *)u, tg->mean, tg->prec, tg->X, tg->y, (void *)base);
         pmcmc_status gs = build_loop_graph(c, kb, tg, o, A, p, w, s_out, s0, max_iters, spin);
+        if (gs == PMCMC_OK && res_dev) {  // enqueue only: the result lands in device memory
+            loop_init_kernel<<<1, 1, 0, st>>>(c->ctl);
+            PM_CUDA(c, cudaGetLastError());
+            PM_CUDA(c, cudaGraphLaunch(c->graph_exec, st));
+            write_result_kernel<<<1, 1, 0, st>>>(c->ctl, T, res_dev);
+            PM_CUDA(c, cudaGetLastError());
+            return PMCMC_OK;
+        }
         if (gs == PMCMC_OK) {
             PM_CUDA(c, cudaEventRecord(c->ev0, st));
             loop_init_kernel<<<1, 1, 0, st>>>(c->ctl);
@@ -728,6 +776,9 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         }
         c->no_graph = 1;  // conditional graphs refused: use the host-driven loop from now on
     }
+    if (res_dev)
+        return fail(c, PMCMC_EUNSUPPORTED, "async solve needs the device-side loop (conditional CUDA graphs, "
+                                          "profiling off)");
     PM_CUDA(c, cudaEventRecord(c->ev0, st));
     int it = 0;
     bool converged = false;

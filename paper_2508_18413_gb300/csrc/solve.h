@@ -78,7 +78,8 @@ pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opt
 void fill_eval_args(EvalArgs &A, const pmcmc_target *tg, const pmcmc_options *o, int T);
 pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
                           const void *s0, const void *s_init, const void *xi, const double *u,
-                          void *s_out, pmcmc_result *res, void *stream);
+                          void *s_out, pmcmc_result *res, void *stream,
+                          pmcmc_result *res_dev = nullptr);
 pmcmc_status window_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_options *o, int T,
                           const void *s0, const void *s_init, const void *xi, const double *u,
                           void *s_out, pmcmc_result *res, void *stream);
