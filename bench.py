@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--workload", default="c2",
                     choices=["c2", "c1", "c3_diag", "c3_bf16", "c3_block", "c4", "c5",
-                             "gibbs_diag", "gibbs_dense", "adjoint_small",
+                             "gibbs_diag", "gibbs_dense", "adjoint_small", "c3_paper",
                              "scan_sweep"],
                     help="c2 (default) is the headline line; the others measure the other "
                          "configurations")
@@ -480,6 +480,27 @@ def run_other(args):
         line.update(config=f"{c.name} {wl}", value=c.T / (ms / 1e3), ms_per_step=ms,
                     newton_iters=res["iters"], status=res["status"], accept_rate=res["accept_rate"],
                     dtype="f32", seq_gpu={"value": c.T / (sms / 1e3), "ms": sms, "speedup": sms / ms})
+    elif wl == "c3_paper":
+        # the banana target with the paper's own HMC setting for its Figure 1 example (App. B.4:
+        # L = 8, step 0.5, the dense Newton Jacobian scaled by 0.5 and clipped to [-1, 1])
+        c = W.C3
+        xi, u = W.noise(c.T, 2, seed=0, dtype=np.float32)
+        tgt = P.Target("banana", 2)
+        s0 = torch.zeros(2, dtype=torch.float32, device=dev)
+        xid, ud = torch.tensor(xi, device=dev), torch.tensor(u, device=dev)
+        opt = P.Options(sampler="hmc", step=0.5, leapfrog_L=8, jac="dense", damping=0.5, clip=1,
+                        precision="f32", atol=c.tol, rtol=c.rtol)
+        ms, (s, res) = _timed(lambda: P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud), args.steps,
+                              args.warmup, flush, stream, torch)
+        sopt = P.Options(sampler="hmc", step=0.5, leapfrog_L=8, precision="f32")
+        sms, (sq, _) = _timed(lambda: P.pmcmc_seq_solve(tgt, sopt, c.T, s0, xid, ud), 1, 1, flush,
+                              stream, torch)
+        dev_max = float(((s - sq).abs() / (1 + sq.abs())).max().item())
+        line.update(config="hmc_banana_l8_step0.5_t100000 dense damping 0.5 clip", value=c.T / (ms / 1e3),
+                    ms_per_step=ms, newton_iters=res["iters"], status=res["status"],
+                    accept_rate=res["accept_rate"], dtype="f32",
+                    max_rel_dev_from_sequential=dev_max,
+                    seq_gpu={"value": c.T / (sms / 1e3), "ms": sms, "speedup": sms / ms})
     elif wl in ("gibbs_diag", "gibbs_dense"):
         c = W.GIBBS
         S = (c.D - 2) // 2
