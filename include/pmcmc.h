@@ -272,7 +272,8 @@ pmcmc_status pmcmc_adjoint(pmcmc_ctx *ctx, const pmcmc_target *target, const pmc
  * calls that overlap on the GPU race, so order them on one stream.  The call is asynchronous
  * and does not report device-side look-back timeouts.
  * Returns EINVAL for bad arguments and EUNSUPPORTED when D > 256 or the scan's scratch
- * (about 4 + 3 D r bytes per tile of ~4096/D timesteps, r = 4 or 8) exceeds 8 MiB.
+ * (about 4 + 3 D r bytes per tile, r = 4 or 8, tiles of about 3300 to 4200 elements for
+ * D <= 32, 4096 / D timesteps above) exceeds 8 MiB.
  */
 pmcmc_status pmcmc_scan_noalloc(pmcmc_precision precision, int T, int D, const void *a,
                                 const void *b, void *s, void *stream);
