@@ -670,3 +670,19 @@ def test_gibbs_deer_reaches_sequential_trace(jac):
     s, iters, conv, _ = O.deer(p, T, s0, kind=jac, atol=1e-9, rtol=1e-12)
     assert conv and iters <= T
     np.testing.assert_allclose(s, ref, rtol=1e-8, atol=1e-8)
+
+
+@pytest.mark.parametrize("jac", ["dense", "diag", "zero"])
+def test_gibbs_deer_prefix_is_exact_after_k_iterations(jac):
+    """After k Newton updates from s_t = s_0, the first k sweeps equal the sequential chain
+    (Section 2's induction), for the Gibbs sweep as for the other samplers."""
+    S, N, T = 4, 9, 30
+    X = W.schools_data(S, N, seed=5)
+    p = O.Problem(O.Target("schools", 2 + 2 * S, X=X), "gibbs", 0.0,
+                  xi=W.gibbs_noise(T, S, N, seed=6), u=np.full(T, 0.5))
+    s0 = W.schools_init(X)
+    ref, _, _ = O.chain(p, T, s0)
+    for k in range(1, 6):
+        s, iters, _, _ = O.deer(p, T, s0, kind=jac, max_iters=k, atol=-1.0)
+        assert iters == k
+        np.testing.assert_allclose(s[:k], ref[:k], rtol=1e-11, atol=1e-11)
