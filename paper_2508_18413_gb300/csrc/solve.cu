@@ -1,6 +1,8 @@
 // Host side of libpmcmc: context, workspace, the C ABI of include/pmcmc.h and the Newton loop
-// of Algorithm 1.  Every arithmetic step runs in the kernels; this file only sizes buffers,
-// launches, and reads back the per-iteration statistics.
+// of Algorithm 1 (on the device in a conditional CUDA graph, host-driven where graphs are not
+// available, or over sliding windows as in Section 3.4).  Every arithmetic step runs in the
+// kernels; this file only sizes buffers, launches, and reads back the per-iteration statistics
+// (or, for the asynchronous solve, has a kernel write them to device memory).
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
