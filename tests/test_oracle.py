@@ -686,3 +686,17 @@ def test_gibbs_deer_prefix_is_exact_after_k_iterations(jac):
         s, iters, _, _ = O.deer(p, T, s0, kind=jac, max_iters=k, atol=-1.0)
         assert iters == k
         np.testing.assert_allclose(s[:k], ref[:k], rtol=1e-11, atol=1e-11)
+
+
+def test_gibbs_noise_distributions():
+    """The Gibbs reparameterisation inputs: Inv-chi^2(nu, 1) base variates (scipy's inverse gamma
+    with shape nu / 2 and scale nu / 2) for the variances, standard normals for the locations."""
+    S, N, T = 5, 11, 20000
+    xi = W.gibbs_noise(T, S, N, seed=3)
+    nu_t, nu_s = 0.1 + S + 1, 0.1 + N
+    crit = 1.95 / np.sqrt(T)
+    assert stats.kstest(xi[:, 0], stats.invgamma(a=nu_t / 2, scale=nu_t / 2).cdf).statistic < crit
+    for k in range(1, 2 + S):
+        assert stats.kstest(xi[:, k], stats.norm.cdf).statistic < crit
+    for k in range(2 + S, 2 + 2 * S):
+        assert stats.kstest(xi[:, k], stats.invgamma(a=nu_s / 2, scale=nu_s / 2).cdf).statistic < crit
