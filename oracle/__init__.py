@@ -292,3 +292,33 @@ def linear_recursion(A, b, dense: bool):
     _load().o_linear_recursion(C.c_int(T), C.c_int(n), C.c_int(int(dense)), _ptr(A), _ptr(b),
                                _ptr(out))
     return out
+
+
+# ---- stochastic diagonal (Section 3.4, Eq. 9) -------------------------------------------------
+
+def hutchinson_probe(seed: int, chain_id: int, t: int, it: int, D: int) -> np.ndarray:
+    """Rademacher probe z (D values in {-1, +1}) of step t (0-based) at Newton iteration `it`.
+
+    The library's counter convention: coordinate d takes bit d mod 32 of output word
+    (d mod 128) div 32 of Philox4x32-10 at counter (d div 128, t, chain_id, 2 + it) under the
+    key (low, high 32 bits of seed); a set bit is +1, a clear bit -1.  Philox itself is the
+    known-answer-pinned generator of this module."""
+    z = np.empty(D)
+    key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+    words = {}
+    for d in range(D):
+        blk = d >> 7
+        if blk not in words:
+            words[blk] = philox4x32_10([blk, t & 0xFFFFFFFF, chain_id & 0xFFFFFFFF,
+                                        (2 + it) & 0xFFFFFFFF], key)
+        w = int(words[blk][(d & 127) >> 5])
+        z[d] = 1.0 if (w >> (d & 31)) & 1 else -1.0
+    return z
+
+
+def hutchinson_diag(p: Problem, t: int, s_prev, z) -> np.ndarray:
+    """One-sample stochastic estimate of diag(J_t) (Eq. 9): z (.) (J_t z), with J_t the dense
+    Newton Jacobian of step t (1-based) at s_prev and z a probe.  Over all sign vectors z its
+    mean is diag(J_t) exactly (E[z_i z_j] = [i = j])."""
+    z = _arr(z)
+    return z * (jacobian(p, t, s_prev, "dense") @ z)

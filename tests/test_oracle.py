@@ -238,6 +238,48 @@ def test_leapfrog_is_eq7():
     np.testing.assert_allclose(O.leapfrog(t, 0.05, s)[:2], xp, rtol=1e-15)
 
 
+def test_leapfrog_on_a_gaussian_is_the_linear_map_of_eq7():
+    """On a Gaussian target grad log p(x) = -P (x - mu) is affine, so one leapfrog step
+    (x' = x + eps v, v' = v + eps grad log p(x')) is the linear map
+    [[I, eps I], [-eps P, I - eps^2 P]] on (x - mu, v).  A sign or argument error in the
+    velocity update (v' from grad log p at x instead of x', or v' = v - eps grad) fails it."""
+    t, mu, _ = gauss(D=3, seed=11)
+    P_ = t.P
+    eps = 0.07
+    I = np.eye(3)
+    M = np.block([[I, eps * I], [-eps * P_, I - eps * eps * P_]])
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        s = rng.standard_normal(6) * 2.0
+        want = M @ np.concatenate([s[:3] - mu, s[3:]]) + np.concatenate([mu, np.zeros(3)])
+        np.testing.assert_allclose(O.leapfrog(t, eps, s), want, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "banana"])
+def test_leapfrog_steps_reproduce_the_hmc_proposal(kind):
+    """Algorithm 2 with the half-step bookkeeping of Appendix A.2: L leapfrog steps from
+    [x_0, v_0 + (eps/2) grad log p(x_0)], then v_L - (eps/2) grad log p(x_L), give the HMC
+    proposal; with u -> 0 (always accept) the moment-pinned HMC step returns that proposal, and
+    its energy change H_0 - H_L follows from the final (x_L, v_L)."""
+    t = gauss(D=3, seed=2)[0] if kind == "gaussian" else O.Target("banana", 2)
+    eps, L = (0.1, 7) if kind == "gaussian" else (0.05, 16)
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        x0 = rng.standard_normal(t.D) + (np.array([0.0, 9.0]) if kind == "banana" else 0.0)
+        v0 = rng.standard_normal(t.D)
+        s = np.concatenate([x0, v0 + 0.5 * eps * O.grad(t, x0)])
+        for _k in range(L):
+            s = O.leapfrog(t, eps, s)
+        xL = s[:t.D]
+        vL = s[t.D:] - 0.5 * eps * O.grad(t, xL)
+        out, dH, acc = O.hmc_step(t, eps, L, x0, v0, 1e-300)
+        assert acc
+        np.testing.assert_allclose(out, xL, rtol=1e-12, atol=1e-12)
+        H0 = 0.5 * v0 @ v0 - O.logp(t, x0)
+        HL = 0.5 * vL @ vL - O.logp(t, xL)
+        assert dH == pytest.approx(H0 - HL, rel=1e-10, abs=1e-10)
+
+
 # ------------------------------------------------------------------------------------------
 # Newton Jacobians (L2)
 # ------------------------------------------------------------------------------------------
@@ -355,6 +397,58 @@ def test_leapfrog_jacobian_and_block_form():
     Jd = O.jacobian(p, 1, s, "diag")
     np.testing.assert_array_equal(np.diag(Jd), np.diag(J))
     assert np.count_nonzero(Jd - np.diag(np.diag(Jd))) == 0
+
+
+@pytest.mark.parametrize("kind,sampler", [("gaussian", "mala"), ("logreg", "mala"),
+                                          ("banana", "mala"), ("banana", "hmc"),
+                                          ("gaussian", "hmc")])
+def test_hutchinson_estimate_is_unbiased_by_enumeration(kind, sampler):
+    """Eq. 9: E_z[z (.) (J z)] = diag J for Rademacher z.  The mean over all 2^D sign vectors is
+    exact, so it must equal the diagonal of the Jacobian, which the finite-difference pins above
+    fix; a probe applied on the wrong side (z (.) J^T z has the same mean, so also check one z by
+    hand), a dropped z factor or a transposed operand fails it."""
+    import itertools
+    if kind == "gaussian":
+        t = gauss(D=3, seed=8)[0]
+    elif kind == "logreg":
+        t = small_logreg(N=30, D=4, seed=6)
+    else:
+        t = O.Target("banana", 2)
+    D = t.D
+    rng = np.random.default_rng(17)
+    eps, L = (0.2, 0) if sampler == "mala" else (0.05, 5)
+    for trial in range(3):
+        x = rng.standard_normal(D) + (np.array([0.0, 9.0]) if kind == "banana" else 0.0)
+        xi = rng.standard_normal(D)
+        u = rng.uniform(0.05, 0.95)
+        p = O.Problem(t, sampler, eps, xi=xi[None, :], u=np.array([u]), L=L)
+        Jd = O.jacobian(p, 1, x, "dense")
+        est = np.zeros(D)
+        for signs in itertools.product([-1.0, 1.0], repeat=D):
+            est += O.hutchinson_diag(p, 1, x, np.array(signs))
+        est /= 2 ** D
+        np.testing.assert_allclose(est, np.diag(Jd), rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(np.diag(O.jacobian(p, 1, x, "diag")), np.diag(Jd),
+                                   rtol=1e-13, atol=1e-13)
+        z = np.where(rng.random(D) < 0.5, -1.0, 1.0)
+        by_hand = np.array([z[i] * sum(Jd[i, j] * z[j] for j in range(D)) for i in range(D)])
+        np.testing.assert_allclose(O.hutchinson_diag(p, 1, x, z), by_hand, rtol=1e-14, atol=1e-14)
+
+
+def test_hutchinson_probe_is_rademacher_from_philox():
+    """The probe's signs are balanced and independent across coordinates, steps and Newton
+    iterations (they come from distinct Philox counters), and coordinate d >= 128 moves to the
+    next counter block."""
+    Z = np.array([O.hutchinson_probe(0xABCDEF0123, 3, t, 0, 40) for t in range(400)])
+    assert set(np.unique(Z)) == {-1.0, 1.0}
+    assert abs(Z.mean()) < 0.03
+    C_ = np.corrcoef(Z.T)
+    assert np.max(np.abs(C_ - np.eye(40))) < 0.25
+    z0 = O.hutchinson_probe(5, 0, 7, 0, 200)
+    z1 = O.hutchinson_probe(5, 0, 7, 1, 200)
+    assert np.mean(z0 == z1) < 0.7              # a new probe per Newton iteration
+    w = O.philox4x32_10([1, 7, 0, 2], [5, 0])   # coordinate 130 = bit 2 of word 0, block 1
+    assert z0[130] == (1.0 if (int(w[0]) >> 2) & 1 else -1.0)
 
 
 def test_damping_and_clip():
