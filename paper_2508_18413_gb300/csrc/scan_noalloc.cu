@@ -10,7 +10,9 @@
 // every GPU that loads the library holds until the process exits.
 //
 // Set-up: the first call on each device (with that device current) resolves the array's device
-// address with cudaGetSymbolAddress; make that first call before any stream capture.  Each call
+// address with cudaGetSymbolAddress; make that first call before any stream capture.  The
+// address is cached per device ordinal for the life of the process, so it assumes the device's
+// primary context (the runtime API's) and no cudaDeviceReset in between.  Each call
 // then clears the parts that must start at zero (the tile flags of this call and the ticket,
 // done and timeout words) with cudaMemsetAsync on the caller's stream, and launches the same
 // scan kernel pmcmc_scan uses.  All calls share the array and each overwrites what the previous
@@ -92,6 +94,10 @@ extern "C" pmcmc_status pmcmc_scan_noalloc(pmcmc_precision prec, int T, int D, c
     w.ctl = ctl;
     cudaError_t e = launch_scan_diag(f64, prec == PMCMC_F32_SCAN_BF16 ? 1 : 0, T, D, tile_t, a, b, s,
                                      nullptr, w, nullptr, nullptr, kDefaultSpinLimit, st);
+    if (e == cudaErrorInvalidValue) {  // a kernel's own tile-count guard refused the size
+        cudaGetLastError();
+        return PMCMC_EUNSUPPORTED;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return PMCMC_ECUDA;
