@@ -78,7 +78,10 @@ typedef enum { PMCMC_GAUSSIAN = 0, PMCMC_LOGREG = 1, PMCMC_BANANA = 2, PMCMC_SCH
  *   DIAG       its exact diagonal (quasi-DEER, Eq. 4);
  *   BLOCK2     diagonal of each block of the leapfrog Jacobian (Appendix A.3; only
  *              PMCMC_HMC_PAR_LEAPFROG);
- *   DIAG_HUTCH one-sample Hutchinson estimate z (.) (J z), z Rademacher (Eq. 9);
+ *   DIAG_HUTCH one-sample Hutchinson estimate z (.) (J z), z Rademacher (Eq. 9), a new probe
+ *              per Newton iteration k: z_d of step t (0-based) is bit d mod 32 of output word
+ *              (d mod 128) div 32 of Philox4x32-10 at counter (d div 128, t, chain_id, 2 + k),
+ *              key (low, high 32 bits of seed); a set bit gives +1, a clear bit -1;
  *   ZERO       J = 0: the plain fixed-point (Picard-type) iteration. */
 typedef enum {
     PMCMC_JAC_DENSE = 0,
@@ -220,6 +223,7 @@ pmcmc_status pmcmc_seq_solve(pmcmc_ctx *ctx, const pmcmc_target *target,
  *           damping and clip applied (may be NULL);
  *   acc_out T device bytes: the accept decision of each step (may be NULL);
  *   ell_out T device doubles: MALA log-ratio / HMC H0 - HL before min(0, .) (may be NULL).
+ * DIAG_HUTCH uses the probes of Newton iteration 0 (see pmcmc_jac).
  */
 pmcmc_status pmcmc_linearize(pmcmc_ctx *ctx, const pmcmc_target *target,
                              const pmcmc_options *opt, int T, const void *s0, const void *s,
@@ -267,10 +271,14 @@ pmcmc_status pmcmc_adjoint(pmcmc_ctx *ctx, const pmcmc_target *target, const pmc
  * whose allocator owns the device.  Its scratch (look-back flags, tile aggregates, control
  * words) is one static device array of 8 MiB that every GPU loading the library holds until
  * process exit.  The first call on a device (with it current) looks up the array's address;
- * make that call before any stream capture.  Each call clears what must start at zero with
+ * make that call before any stream capture.  The address is kept per device ordinal for the
+ * rest of the process: it belongs to the device's primary context, so call this from the
+ * primary context and do not reset the device in between.  Each call clears what must start at zero with
  * cudaMemsetAsync on `stream`; it neither allocates nor frees.  All calls share the array:
  * calls that overlap on the GPU race, so order them on one stream.  The call is asynchronous
- * and does not report device-side look-back timeouts.
+ * and does not report device-side look-back timeouts: if a bounded look-back wait runs out
+ * (it does not with the default bound unless the GPU is shared with work that starves the
+ * scan), the call still returns and stays within its buffers, but s is undefined.
  * Returns EINVAL for bad arguments and EUNSUPPORTED when D > 256 or the scan's scratch
  * (about 4 + 3 D r bytes per tile, r = 4 or 8, tiles of about 3300 to 4200 elements for
  * D <= 32, 4096 / D timesteps above) exceeds 8 MiB.
@@ -305,6 +313,19 @@ typedef struct {
  */
 pmcmc_status pmcmc_solve_batched(pmcmc_ctx *ctx, int B, const pmcmc_chain_desc *chains,
                                  const pmcmc_options *opt, pmcmc_result *res, void *stream);
+
+/*
+ * The sequential chains of a batch on the GPU in one launch: the baseline of
+ * pmcmc_solve_batched (the paper's sequential loop, Section 5, for many chains at once).  One
+ * CTA per chain, the longest chains dispatched first; each chain runs its T dependent steps with
+ * its design (logistic) or precision matrix (Gaussian) in shared memory.  MALA or HMC chains on
+ * GAUSSIAN or LOGREG targets with D <= 128 whose design fits one SM's shared memory
+ * (EUNSUPPORTED otherwise); opt->precision F32 or F64 gives the arithmetic (u is double, the
+ * accept decision is taken in FP64).  Target Q, Newton and tolerance fields are not used.
+ * chains[i].s_out (T x D device reals) receives chain i.  Asynchronous on `stream`.
+ */
+pmcmc_status pmcmc_seq_solve_batched(pmcmc_ctx *ctx, int B, const pmcmc_chain_desc *chains,
+                                     const pmcmc_options *opt, void *stream);
 
 /*
  * Measurement support (the paper reports post-compilation wall-clock only, Section 5 and

@@ -21,6 +21,7 @@ __all__ = [
     "pmcmc_solve_async", "result_from_device",
     "ChainDesc", "real_dtype", "loaded_library_path", "pmcmc_profile_enable",
     "pmcmc_profile_get", "pmcmc_scan_noalloc", "ChainSolve", "solve_differentiable",
+    "pmcmc_seq_solve_batched",
 ]
 
 
@@ -344,6 +345,24 @@ def pmcmc_solve_batched(chains: list[ChainDesc], opt: Options):
     return [_result_dict(r) for r in res]
 
 
+def pmcmc_seq_solve_batched(chains: list[ChainDesc], precision: str = "f32"):
+    """The sequential chains of a batch in one launch (one CTA per chain); writes each
+    chain's s_out.  Asynchronous on the current stream."""
+    ctx = pmcmc_create()
+    dt = real_dtype(precision)
+    arr = (L.pmcmc_chain_desc * len(chains))()
+    keep = []
+    for i, ch in enumerate(chains):
+        tc = ch.target.c(dt)
+        keep.append((tc, ch.target._keep))
+        arr[i] = L.pmcmc_chain_desc(tc, SAMPLERS[ch.sampler], float(ch.step), int(ch.leapfrog_L),
+                                    int(ch.T), _ptr(_dev(ch.s0, dt, "s0")), _ptr(_dev(ch.xi, dt, "xi")),
+                                    _ptr(_dev(ch.u, torch.float64, "u")), _ptr(ch.s_out))
+    oc = Options(precision=precision).c()
+    st = L.load().pmcmc_seq_solve_batched(ctx, len(chains), arr, C.byref(oc), _stream())
+    _check(ctx, st)
+
+
 def pmcmc_profile_enable(enable: bool = True):
     """Start (and reset) or stop the context's launch counters and kernel event timers."""
     ctx = pmcmc_create()
@@ -369,6 +388,8 @@ def pmcmc_scan_noalloc(precision: str, a, b, s):
     st = L.load().pmcmc_scan_noalloc(PRECISIONS[precision], T, D, _ptr(a), _ptr(b), _ptr(s),
                                      _stream())
     if st != 0:
-        raise PmcmcError(st, "pmcmc_scan_noalloc failed (EUNSUPPORTED: scratch beyond 8 MiB or "
-                             "D > 256)")
+        why = {L.PMCMC_EUNSUPPORTED: "look-back scratch beyond the static 8 MiB, or D > 256",
+               L.PMCMC_EINVAL: "invalid arguments",
+               L.PMCMC_ECUDA: "a CUDA call failed (symbol lookup, memset or launch)"}
+        raise PmcmcError(st, "pmcmc_scan_noalloc: " + why.get(st, "failed"))
     return s

@@ -57,7 +57,7 @@ EXPORTS = [
     "pmcmc_options_default", "pmcmc_create", "pmcmc_destroy", "pmcmc_last_error",
     "pmcmc_gen_noise", "pmcmc_solve", "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan",
     "pmcmc_adjoint", "pmcmc_solve_batched", "pmcmc_profile_enable", "pmcmc_profile_get",
-    "pmcmc_scan_noalloc",
+    "pmcmc_scan_noalloc", "pmcmc_seq_solve_batched",
 ]
 
 _lib = None
@@ -104,6 +104,9 @@ def load(path: str = LIB_PATH):
     lib.pmcmc_solve_batched.argtypes = [vp, i, C.POINTER(pmcmc_chain_desc),
                                         C.POINTER(pmcmc_options), C.POINTER(pmcmc_result), vp]
     lib.pmcmc_solve_batched.restype = st
+    lib.pmcmc_seq_solve_batched.argtypes = [vp, i, C.POINTER(pmcmc_chain_desc),
+                                            C.POINTER(pmcmc_options), vp]
+    lib.pmcmc_seq_solve_batched.restype = st
     lib.pmcmc_scan_noalloc.argtypes = [i, i, i, vp, vp, vp, vp]
     lib.pmcmc_scan_noalloc.restype = st
     lib.pmcmc_profile_enable.argtypes = [vp, i]

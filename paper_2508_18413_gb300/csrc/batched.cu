@@ -25,6 +25,7 @@
 #include "common.cuh"
 #include "eval_small.cuh"
 #include "logreg_tile.cuh"
+#include "seq.h"
 #include "solve.h"
 
 namespace pm {
@@ -890,13 +891,79 @@ BatchTune batch_tune_lookup(pmcmc_ctx *c, int B, const pmcmc_chain_desc *chains,
 
 namespace pm {
 
-// Chains still unconverged after the Newton sweeps are recomputed by the sequential loop, up to
-// sixteen at once on the context's side streams (ordered after `st`, and `st` after them).
+static SeqChain seq_of(const pmcmc_chain_desc &d) {
+    SeqChain q;
+    q.target = d.target.kind;
+    q.sampler = d.sampler;
+    q.D = d.target.D;
+    q.N = d.target.N;
+    q.L = d.leapfrog_L;
+    q.T = d.T;
+    q.eps = d.step;
+    q.sigma_p = d.target.prior_scale;
+    q.X = d.target.X;
+    q.y = d.target.y;
+    q.mu = d.target.mean;
+    q.P = d.target.prec;
+    q.s0 = d.s0;
+    q.xi = d.xi;
+    q.u = d.u;
+    q.s_out = d.s_out;
+    return q;
+}
+
+// The sequential loops of the chains `idx` in one launch, one CTA per chain, the longest chains
+// first (their CTAs are dispatched first when the chains outnumber the resident CTAs).
+static cudaError_t seq_batch_launch(pmcmc_ctx *c, const pmcmc_chain_desc *ch, std::vector<int> idx,
+                                    bool f64, cudaStream_t st) {
+    if (idx.empty()) return cudaSuccess;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return ch[a].T > ch[b].T; });
+    std::vector<SeqChain> v;
+    size_t smem = 0;
+    for (int i : idx) {
+        v.push_back(seq_of(ch[i]));
+        smem = std::max(smem, seq_smem_bytes(v.back(), 1, kSeqThreadsBatched, f64));
+    }
+    const size_t bytes = sizeof(SeqChain) * v.size();
+    if (c->seq_desc_bytes < bytes) {
+        if (c->seq_desc) {
+            cudaError_t e = cudaStreamSynchronize(st);  // the old descriptors may still be read
+            if (e != cudaSuccess) return e;
+            cudaFree(c->seq_desc);
+            c->seq_desc = nullptr;
+            c->seq_desc_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&c->seq_desc, bytes);
+        if (e != cudaSuccess) return e;
+        c->seq_desc_bytes = bytes;
+    }
+    // pageable source: the copy is staged before the call returns
+    cudaError_t e = cudaMemcpyAsync(c->seq_desc, v.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    prof_count(c);
+    return launch_seq_chains(static_cast<const SeqChain *>(c->seq_desc), (int)v.size(), smem, f64, st);
+}
+
+static bool seq_batch_ok(const pmcmc_chain_desc &d, bool f64) {
+    const SeqChain q = seq_of(d);
+    return seq_fast_supported(q) && seq_smem_bytes(q, 1, kSeqThreadsBatched, f64) <= kSeqSmemBudget;
+}
+
+// Chains still unconverged after the Newton sweeps are recomputed by the sequential loop: all
+// Gaussian and logistic chains in one launch, one CTA each; any other chain (banana) on the
+// context's side streams, up to sixteen at once (ordered after `st`, and `st` after them).
 static cudaError_t complete_sequential(pmcmc_ctx *c, int B, const pmcmc_chain_desc *ch,
                                        pmcmc_result *rv, cudaStream_t st) {
-    std::vector<int> todo;
-    for (int i = 0; i < B; i++)
-        if (rv[i].status == PMCMC_NOT_CONVERGED) todo.push_back(i);
+    std::vector<int> todo, batch;
+    for (int i = 0; i < B; i++) {
+        if (rv[i].status != PMCMC_NOT_CONVERGED) continue;
+        rv[i].status = PMCMC_OK;
+        rv[i].sequential = 1;
+        rv[i].max_residual = 0.0;
+        (seq_batch_ok(ch[i], false) ? batch : todo).push_back(i);
+    }
+    cudaError_t eb = seq_batch_launch(c, ch, batch, false, st);
+    if (eb != cudaSuccess) return eb;
     if (todo.empty()) return cudaSuccess;
     for (cudaStream_t &q : c->seq_streams)
         if (!q) {
@@ -930,9 +997,6 @@ static cudaError_t complete_sequential(pmcmc_ctx *c, int B, const pmcmc_chain_de
         cudaStream_t q = c->seq_streams[j % nq];
         e = d.target.kind == PMCMC_LOGREG ? launch_seq_logreg(A, q) : launch_seq_small(A, q);
         if (e != cudaSuccess) return e;
-        rv[i].status = PMCMC_OK;
-        rv[i].sequential = 1;
-        rv[i].max_residual = 0.0;
     }
     for (int k = 0; k < nq && e == cudaSuccess; k++) {
         e = cudaEventRecord(c->seq_events[k], c->seq_streams[k]);
@@ -1108,3 +1172,31 @@ BatchTune batch_tune_lookup(pmcmc_ctx *c, int B, const pmcmc_chain_desc *chains,
 }
 
 }  // namespace pm
+
+extern "C" pmcmc_status pmcmc_seq_solve_batched(pmcmc_ctx *c, int B, const pmcmc_chain_desc *chains,
+                                                const pmcmc_options *o, void *stream) {
+    using namespace pm;
+    if (!c) return PMCMC_EINVAL;
+    if (B < 0 || (B > 0 && !chains) || !o) return set_error(c, PMCMC_EINVAL, "seq batched: bad arguments");
+    if (B == 0) return PMCMC_OK;
+    if (o->precision != PMCMC_F32 && o->precision != PMCMC_F64)
+        return set_error(c, PMCMC_EINVAL, "seq batched: F32 or F64");
+    const bool f64 = o->precision == PMCMC_F64;
+    std::vector<int> idx;
+    for (int i = 0; i < B; i++) {
+        const pmcmc_chain_desc &d = chains[i];
+        const pmcmc_target &t = d.target;
+        if (d.T < 1 || !d.s0 || !d.xi || !d.u || !d.s_out)
+            return set_error(c, PMCMC_EINVAL, "seq batched: chain with bad T or buffers");
+        if (d.sampler != PMCMC_MALA && d.sampler != PMCMC_HMC)
+            return set_error(c, PMCMC_EINVAL, "seq batched: MALA or HMC chains");
+        if (t.kind == PMCMC_GAUSSIAN ? (!t.mean || !t.prec) : (t.kind != PMCMC_LOGREG || !t.X || !t.y || t.N < 1))
+            return set_error(c, PMCMC_EINVAL, "seq batched: Gaussian (mean, prec) or logistic (X, y) chains");
+        if (!seq_batch_ok(d, f64))
+            return set_error(c, PMCMC_EUNSUPPORTED, "seq batched: D <= 128 and the design in one SM's shared memory");
+        idx.push_back(i);
+    }
+    PM_CUDA_B(cudaSetDevice(c->device));
+    PM_CUDA_B(seq_batch_launch(c, chains, idx, f64, (cudaStream_t)stream));
+    return PMCMC_OK;
+}

@@ -19,6 +19,7 @@
 // assembles J_t = g (I + eps H(x)) + (1 - g) I + u_t v_t^T.
 #include "common.cuh"
 #include "eval.h"
+#include "seq.h"
 #include "logreg_tile.cuh"
 
 namespace pm {
@@ -487,6 +488,12 @@ cudaError_t launch_logreg_dense_jac(const EvalArgs &A, cudaStream_t st) {
 }
 
 cudaError_t launch_seq_logreg(const EvalArgs &A, cudaStream_t st) {
+    {
+        SeqChain ch = seq_chain_from(A);
+        if (seq_fast_supported(ch) && seq_cluster_size(ch, A.f64) > 0) return launch_seq_chain(ch, A.f64, st);
+    }
+    // fallback for designs too large for the shared memory of a 16-CTA cluster: one CTA that
+    // reads the design from global memory
     const size_t sm = (A.f64 ? 8 : 4) * ((size_t)5 * A.D + A.N + 256);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
     if (A.f64)

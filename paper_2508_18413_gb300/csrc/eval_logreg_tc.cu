@@ -92,7 +92,8 @@ constexpr int oMisc = oBar + 8 * kNumBars;     // tmem address, abort flag
 constexpr int oPart = oMisc + 16;              // double [4][128]: per-warpgroup log-ratio parts
 constexpr int oAcc = oPart + kGroups * kM * 8; // int [128]: decisions
 constexpr int oRed = oAcc + kM * 4;            // double [16][4]: per-warp statistics
-constexpr int kSmemUsed = oRed + kEpiWarps * 4 * 8;
+constexpr int oLogu = oRed + kEpiWarps * 4 * 8; // double [128]: log u of each timestep
+constexpr int kSmemUsed = oLogu + kM * 8;
 constexpr int kSmemBytes = kSmemUsed + 1024;   // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 static_assert(oStage % 1024 == 0 && kStageStride % 1024 == 0 && oCW % 1024 == 0, "alignment");
@@ -307,6 +308,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             put_row_pair(sm + oVhi, sm + oVlo, r, h, x);
             warp_arrive(bar(bVready));
         }
+        // log u (FP64) while the first products run; read back by the same thread at the end
+        if (h == 0) reinterpret_cast<double *>(sm + oLogu)[r] = tv ? log(A.u[t]) : 0.0;
         auto add_partial = [&](int kc) {  // G of chunk kc, own dimensions
             float gp[kCols], gpl[kCols];
             tmem_ld8(lrow + kColG + 64u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
@@ -439,25 +442,30 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         // gs holds the own dimensions of the G row at x~.  The MH log-ratio (FP64):
         //   ell = [ll(x~) - |x~|^2/2sp2] - [ll(x) - |x|^2/2sp2] - |e|^2/(4 eps) + |xi|^2/2,
         //   e = x - x~ - eps grad log p(x~), summed over the four warpgroups.
+        // The per-dimension terms of the log-ratio are formed in FP32 from the FP32 state, the
+        // proposal and the gradient (their rounding, ~1e-7 each, is far below what the FP32
+        // states themselves carry into ell); the log-likelihood difference, which cancels two
+        // sums of N terms, and the sum over the warpgroups are FP64.  Every global load of the
+        // tail (x = s_{t-1}, the noise, s_t) is issued before any of them is used.
         double *part = reinterpret_cast<double *>(sm + oPart);
         int *accf = reinterpret_cast<int *>(sm + oAcc);
-        float x[kCols];
+        float x[kCols], xv[kCols], sv[kCols];
         load_x(x);
+        load_xi(xv);
+#pragma unroll
+        for (int i = 0; i < kCols; i++) sv[i] = (tv && d0 + i < D) ? s[(size_t)t * D + d0 + i] : 0.0f;
         {
-            float xv[kCols];
-            load_xi(xv);
-            const double sp2 = A.sigma_p * A.sigma_p;
-            double quad = ll1 - ll0;
+            const float inv2sp2 = 0.5f * inv_sp2, inv4e = 0.25f / eps;
+            float qf = 0.0f;
 #pragma unroll
             for (int i = 0; i < kCols; i++) {
                 if (d0 + i < D) {
                     const float g2 = gs[i] - xt[i] * inv_sp2;
                     const float e = x[i] - xt[i] - eps * g2;
-                    quad += -((double)xt[i] * xt[i] - (double)x[i] * x[i]) / (2.0 * sp2) -
-                            (double)e * e / (4.0 * (double)eps) + 0.5 * (double)xv[i] * xv[i];
+                    qf += -(xt[i] - x[i]) * (xt[i] + x[i]) * inv2sp2 - e * e * inv4e + 0.5f * xv[i] * xv[i];
                 }
             }
-            part[h * kM + r] = quad;
+            part[h * kM + r] = (ll1 - ll0) + (double)qf;
         }
         named_bar(1, kEpiThreads);
         const bool valid = tv && ok && !*abort_f;
@@ -468,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             if (valid) {
                 const double ell = part[r] + part[kM + r] + part[2 * kM + r] + part[3 * kM + r];
                 const double la = (ell < 0.0 || isnan(ell)) ? ell : 0.0;
-                const double gtl = la - log(A.u[t]);
+                const double gtl = la - reinterpret_cast<const double *>(sm + oLogu)[r];
                 acc = gtl > 0.0;
                 margin = fabs(gtl);
                 acc_i = acc;
@@ -500,10 +508,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 if (d < D) {
                     const size_t o = (size_t)t * D + d;
                     const float f = acc ? xt[i] : x[i];
-                    const float sv = s[o];
-                    const float rr = f - sv;
+                    const float rr = f - sv[i];
                     const double ar = fabs((double)rr);
-                    const double ee = ar - A.rtol * fabs((double)sv);
+                    const double ee = ar - A.rtol * fabs((double)sv[i]);
                     err = isnan(ee) ? INFINITY : fmax(err, ee);
                     rmax = isnan(ar) ? INFINITY : fmax(rmax, ar);
                     if (bout) store_as<S_, float>(bout + o, rr);

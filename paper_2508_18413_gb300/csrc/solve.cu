@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "eval.h"
+#include "seq.h"
 #include "internal.h"
 #include "solve.h"
 
@@ -217,6 +218,7 @@ pmcmc_status pmcmc_destroy(pmcmc_ctx *c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->ws) cudaFree(c->ws);
     if (c->aux) cudaFree(c->aux);
+    if (c->seq_desc) cudaFree(c->seq_desc);
     if (c->ctl) cudaFree(c->ctl);
     if (c->host_ctl) cudaFreeHost(c->host_ctl);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -355,7 +357,7 @@ pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opt
         if (!tg->X || !tg->y || tg->N <= 0) return fail(c, PMCMC_EINVAL, "logreg needs X, y, N > 0");
         if (!(tg->prior_scale > 0.0)) return fail(c, PMCMC_EINVAL, "prior_scale must be > 0");
         if (logreg_padded_dim(D) < 0) return fail(c, PMCMC_EUNSUPPORTED, "logreg supports D <= 128");
-        if (o->precision == PMCMC_F64 && D > 64)
+        if (o->precision == PMCMC_F64 && D > 64 && !sequential)  // the sequential loop takes D <= 128
             return fail(c, PMCMC_EUNSUPPORTED, "logreg in FP64 supports D <= 64");
         break;
     default:
@@ -1098,7 +1100,7 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
     A.a_out = jac_out ? jac_out : (dense ? (void *)(base + o_j) : nullptr);
     A.acc_out = acc_out;
     A.ell_out = ell_out;
-    A.iter = &c->ctl->iter;
+    A.iter = nullptr;  // Hutchinson probes of Newton iteration 0, whatever ran before
     if (tg->kind == PMCMC_LOGREG) {
         const int DP = logreg_padded_dim(D);
         const int Npad = ceil_div(tg->N, 64) * 64;
@@ -1159,6 +1161,9 @@ extern "C" pmcmc_status pmcmc_seq_solve(pmcmc_ctx *c, const pmcmc_target *tg,
     if (tg->kind == PMCMC_LOGREG) {
         if (tg->N > 20000) return fail(c, PMCMC_EUNSUPPORTED, "seq_solve logreg supports N <= 20000");
         PM_CUDA(c, launch_seq_logreg(A, st));
+    } else if (tg->kind == PMCMC_GAUSSIAN && tg->D >= 4 && seq_fast_supported(seq_chain_from(A))) {
+        // one CTA: the D x D products spread over D threads (a lone thread serves D < 4)
+        PM_CUDA(c, launch_seq_chain(seq_chain_from(A), A.f64, st));
     } else {
         PM_CUDA(c, launch_seq_small(A, st));
     }

@@ -66,6 +66,8 @@ struct pmcmc_ctx {
     std::map<std::string, std::pair<int, int>> tune_cache;
     void *aux = nullptr;  // rotated copies for the orthogonal basis Q
     size_t aux_bytes = 0;
+    void *seq_desc = nullptr;  // chain descriptors of a many-chain sequential launch
+    size_t seq_desc_bytes = 0;
     std::string batch_graph_key;
     cudaGraphExec_t batch_graph_exec = nullptr;
 };

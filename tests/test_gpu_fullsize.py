@@ -1,17 +1,19 @@
 """Parity at the workloads' full sizes, in the launch configuration bench.py times.
 
-Two checks per workload:
-  * trace: the GPU fixed point equals the oracle's sequential FP64 trace within
-    1e-5 (1 + |s|) up to the first near-tie decision (oracle margin < 1e-4; past a tie both
-    outcomes are valid chains of the same noise).  This bar needs a residual tolerance below
-    it: a rejected step has J = I, so along a run of rejections the residual left at each step
-    is carried forward undamped and the trace error of an iterate is several times its
-    residual.  The solve at the workload's own tolerance (1e-5) is therefore held to
-    5e-5 (1 + |s|), and the same launch with atol 1e-6 to 1e-5 (1 + |s|);
-  * fixed-point property at every t, which holds at any size and past ties: s_t equals the
-    oracle's transition f_t(s_{t-1}) evaluated at the GPU's own s_{t-1}, within the solve's
-    residual tolerance (atol + rtol |s|) plus the FP32 trace tolerance 1e-5 (1 + |s|); where the
-    oracle's margin is below 1e-4 either branch is accepted.
+Three checks per workload, over the whole chain:
+  * decisions: every accept/reject decision equals the FP64 oracle's, except at a true tie
+    (oracle margin |min(0, ell) - log u| below 1e-9 (1 + |ell|)), where both outcomes are valid
+    chains of the same noise; the ties are listed (none occur on these workloads);
+  * trace: the GPU fixed point equals the oracle's sequential FP64 trace within the FP32 bar
+    at every step (up to the first tie, if any).  The bar needs a residual tolerance below it:
+    a rejected step has J = I, so the residual left at each step of a run of rejections is
+    carried forward undamped and the trace error of an iterate is several times its residual.
+    At atol 1e-6 the headline solve meets 1e-5 (1 + |s|) (measured 1.3e-6); at atol 1e-5 it
+    is held to 5e-5 (1 + |s|) (measured 1.2e-5).  The banana HMC chain is FP32-sensitive (see
+    below): its FP32 bar is the FP32 sequential loop's own deviation, and an FP64 solve is held
+    to 1e-8;
+  * fixed-point property at every t: s_t equals the oracle's transition f_t(s_{t-1}) at the
+    GPU's own s_{t-1}, within the residual tolerance plus the trace bar.
 """
 import numpy as np
 import pytest
@@ -28,33 +30,41 @@ if torch.cuda.is_available():
 DEV = "cuda:0"
 
 
-def _check(ot, sampler, step, L, xi, u, s, s0, atol, rtol, trace_tol):
+TIE = 1e-9   # a true tie: the oracle's decision margin below 1e-9 (1 + |ell|)
+
+
+def _check(ot, sampler, step, L, xi, u, s, acc_gpu, s0, atol, rtol, trace_tol):
+    """Whole-chain comparison.  Decisions must equal the oracle's at every step that is not a
+    true tie; with no tie the trace must match at every step.  Returns (flips, ties, max error,
+    smallest oracle margin)."""
     T = len(s)
     p = O.Problem(ot, sampler, step, xi=xi, u=u, L=L)
     ref, ell, acc = O.chain(p, T, s0)
     margin = np.abs(np.minimum(ell, 0.0) - np.log(u))
-    ties = np.nonzero(margin < 1e-4)[0]
-    upto = ties[0] if len(ties) else T
+    ties = np.nonzero(margin < TIE * (1 + np.abs(ell)))[0]
+    flips = np.nonzero(acc_gpu != acc)[0]
+    assert set(flips.tolist()) <= set(ties.tolist()), (flips[:10], margin[flips[:10]])
+    upto = ties[0] if len(ties) else T       # past a true tie both branches are valid chains
     err = np.abs(s[:upto] - ref[:upto]) / (1 + np.abs(ref[:upto]))
-    assert np.all(err <= trace_tol), (np.max(err), upto)
-    # fixed-point property at every t
+    assert np.all(err <= trace_tol), (float(np.max(err)), int(np.argmax(err.max(axis=1))))
+    # fixed-point property at every t (also past a tie): s_t = f_t(s_{t-1}) at the GPU's s_{t-1}
     bad = 0
     for t in range(T):
         prev = s0 if t == 0 else s[t - 1]
         fo, ello, acco = O.f(p, t + 1, prev)
         m = abs(min(0.0, ello) - np.log(u[t]))
-        ok = np.all(np.abs(s[t] - fo) <= atol + rtol * np.abs(s[t]) + 1e-5 * (1 + np.abs(fo)))
-        if not ok and m < 1e-4:   # the other branch
-            ok = np.all(np.abs(s[t] - prev) <= atol + rtol * np.abs(s[t]) + 1e-5 * (1 + np.abs(prev)))
+        ok = np.all(np.abs(s[t] - fo) <= atol + rtol * np.abs(s[t]) + trace_tol * (1 + np.abs(fo)))
+        if not ok and m < TIE * (1 + abs(ello)):   # the other branch of a tie
+            ok = np.all(np.abs(s[t] - prev) <= atol + rtol * np.abs(s[t]) + trace_tol * (1 + np.abs(prev)))
         bad += not ok
     assert bad == 0, bad
-    return upto
+    return len(flips), ties.tolist(), float(np.max(err)) if upto else 0.0, float(margin.min())
 
 
 @pytest.mark.parametrize("atol,trace_tol", [(1e-5, 5e-5), (1e-6, 1e-5)])
 def test_c2_full_size_matches_oracle(atol, trace_tol):
     """MALA, logistic regression N=1000, D=25, T=16384, step 0.01, FP32, quasi-DEER with the
-    exact diagonal of the held-gate Jacobian, clip, tol 1e-5 (the bench's headline solve)."""
+    exact diagonal of the held-gate Jacobian, clip (the bench's headline solve: atol 1e-6)."""
     c = W.C2
     X, y, _ = W.blr_data(c.N, c.D, seed=c.seed, dtype=np.float32)
     xi, u = W.noise(c.T, c.D, seed=0, dtype=np.float32)
@@ -64,24 +74,72 @@ def test_c2_full_size_matches_oracle(atol, trace_tol):
     opt = P.Options(sampler="mala", step=c.step, jac="diag", precision="f32", atol=atol, clip=1,
                     gate_grad=0)
     s0 = torch.zeros(c.D, dtype=torch.float32, device=DEV)
-    s, res = P.pmcmc_solve(gt, opt, c.T, s0, xi=torch.tensor(xi, device=DEV),
-                           u=torch.tensor(u, device=DEV))
+    xid, ud = torch.tensor(xi, device=DEV), torch.tensor(u, device=DEV)
+    s, res = P.pmcmc_solve(gt, opt, c.T, s0, xi=xid, u=ud)
     assert res["status"] == "OK"
-    upto = _check(ot, "mala", c.step, 0, xi.astype(np.float64), u, s.cpu().double().numpy(),
-                  np.zeros(c.D), atol, 0.0, trace_tol)
-    assert upto >= 1000
+    _, _, acc, _ = P.pmcmc_linearize(gt, P.Options(sampler="mala", step=c.step, jac="zero",
+                                                   precision="f32"), c.T, s0, s, xid, ud,
+                                     want_jac=False)
+    flips, ties, err, _ = _check(ot, "mala", c.step, 0, xi.astype(np.float64), u,
+                                 s.cpu().double().numpy(), acc.cpu().numpy().astype(bool),
+                                 np.zeros(c.D), atol, 0.0, trace_tol)
+    assert ties == [] and flips == 0
 
 
-@pytest.mark.parametrize("atol,rtol,trace_tol", [(1e-5, 1e-5, 5e-5), (1e-6, 1e-6, 1e-5)])
-def test_c3_full_size_matches_oracle(atol, rtol, trace_tol):
+# The banana HMC chain is sensitive to FP32 rounding: the FP32 sequential GPU loop itself
+# (the same chain computed step by step) leaves the FP64 oracle's trace by up to 1.3e-3 (1 + |s|)
+# (step 67,937) with every decision equal, and the oracle's own chain with its state rounded to
+# FP32 after each step drifts by 1.4e-4.  So the FP32 solve is held to the oracle's decisions at
+# every step, to the FP32 sequential loop within 1e-5 (1 + |s|) (same arithmetic, so the
+# difference is the solver's), and to the oracle within the FP32 loop's own deviation, 2e-3;
+# the FP64 solve is held to the oracle's trace within 1e-8 (1 + |s|).
+C3_FP32_SENSITIVITY = 2e-3
+
+
+@pytest.mark.parametrize("atol,rtol", [(1e-5, 1e-5), (1e-6, 1e-6)])
+def test_c3_full_size_matches_oracle(atol, rtol):
     """HMC on the banana, L=16, step 0.05, T=100000, FP32, quasi-DEER diagonal with clip."""
     c = W.C3
     xi, u = W.noise(c.T, 2, seed=0, dtype=np.float32)
     opt = P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, jac="diag", clip=1,
                     precision="f32", atol=atol, rtol=rtol)
     s0 = torch.zeros(2, dtype=torch.float32, device=DEV)
-    s, res = P.pmcmc_solve(P.Target("banana", 2), opt, c.T, s0, xi=torch.tensor(xi, device=DEV),
-                           u=torch.tensor(u, device=DEV))
+    xid, ud = torch.tensor(xi, device=DEV), torch.tensor(u, device=DEV)
+    tgt = P.Target("banana", 2)
+    s, res = P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud)
     assert res["status"] == "OK"
-    _check(O.Target("banana", 2), "hmc", c.step, c.L, xi.astype(np.float64), u,
-           s.cpu().double().numpy(), np.zeros(2), atol, rtol, trace_tol)
+    sq, _ = P.pmcmc_seq_solve(tgt, P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L,
+                                             precision="f32"), c.T, s0, xid, ud)
+    sqh = sq.cpu().double().numpy()
+    sh = s.cpu().double().numpy()
+    vs_seq = np.abs(sh - sqh) / (1 + np.abs(sqh))
+    assert vs_seq.max() <= 5e-5 if atol == 1e-5 else vs_seq.max() <= 1e-5, vs_seq.max()
+    _, _, acc, _ = P.pmcmc_linearize(tgt, P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L,
+                                                    jac="zero", precision="f32"),
+                                     c.T, s0, s, xid, ud, want_jac=False)
+    flips, ties, err, _ = _check(O.Target("banana", 2), "hmc", c.step, c.L, xi.astype(np.float64),
+                                 u, sh, acc.cpu().numpy().astype(bool), np.zeros(2), atol, rtol,
+                                 C3_FP32_SENSITIVITY)
+    assert ties == [] and flips == 0
+
+
+def test_c3_full_size_fp64_matches_oracle():
+    """The same chain solved in FP64: the trace equals the oracle's within 1e-8 (1 + |s|) at every
+    one of the 100,000 steps, every decision equal."""
+    c = W.C3
+    xi, u = W.noise(c.T, 2, seed=0, dtype=np.float32)
+    xi = xi.astype(np.float64)
+    opt = P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, jac="diag", clip=1,
+                    precision="f64", atol=1e-11, rtol=0.0)
+    s0 = torch.zeros(2, dtype=torch.float64, device=DEV)
+    xid, ud = torch.tensor(xi, device=DEV), torch.tensor(u, device=DEV)
+    tgt = P.Target("banana", 2)
+    s, res = P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud)
+    assert res["status"] == "OK"
+    _, _, acc, _ = P.pmcmc_linearize(tgt, P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L,
+                                                    jac="zero", precision="f64"),
+                                     c.T, s0, s, xid, ud, want_jac=False)
+    flips, ties, err, _ = _check(O.Target("banana", 2), "hmc", c.step, c.L, xi, u,
+                                 s.cpu().numpy(), acc.cpu().numpy().astype(bool), np.zeros(2),
+                                 1e-11, 0.0, 1e-8)
+    assert ties == [] and flips == 0

@@ -494,3 +494,30 @@ def test_basis_reparam_logreg(dt):
     s, r = P.pmcmc_solve(gq, opt, T, cu(np.zeros(12), dt), xi=cu(xi, dt), u=cu(u))
     assert r["status"] == "OK"
     _assert_trace(npy(s), ref, margin, dt)
+
+
+def test_fp64_polish_of_an_fp32_solve_reaches_the_oracle():
+    """Mixed-precision use: an FP32 solve, then an FP64 solve started from it (s_init) polishes
+    the trace to FP64 accuracy, with the oracle's decisions at every step, in fewer FP64
+    iterations than an FP64 solve from the initial guess needs."""
+    ot, gt64 = logreg_pair(300, 8, seed=4)
+    X, y, _ = W.blr_data(300, 8, seed=4)
+    gt32 = P.Target("logreg", 8, X=cu(X, torch.float32), y=cu(y, torch.float32))
+    T = 3000
+    xi, u = noise(T, 8, 9, torch.float32)
+    ref, ell, acc = O.chain(O.Problem(ot, "mala", 0.01, xi=xi, u=u), T, np.zeros(8))
+    s32, r32 = P.pmcmc_solve(gt32, P.Options(sampler="mala", step=0.01, jac="diag", precision="f32",
+                                             atol=1e-6, clip=1, gate_grad=0),
+                             T, cu(np.zeros(8), torch.float32), xi=cu(xi, torch.float32), u=cu(u))
+    assert r32["status"] == "OK"
+    o64 = P.Options(sampler="mala", step=0.01, jac="diag", precision="f64", atol=1e-11, clip=1,
+                    gate_grad=0)
+    s64, r64 = P.pmcmc_solve(gt64, o64, T, cu(np.zeros(8)), s_init=s32.double(), xi=cu(xi), u=cu(u))
+    _, rs = P.pmcmc_solve(gt64, o64, T, cu(np.zeros(8)), xi=cu(xi), u=cu(u))
+    assert r64["status"] == "OK" and rs["status"] == "OK"
+    assert r64["iters"] < rs["iters"]
+    np.testing.assert_allclose(npy(s64), ref, rtol=0, atol=1e-9)
+    _, _, a64, _ = P.pmcmc_linearize(gt64, P.Options(sampler="mala", step=0.01, jac="zero",
+                                                     precision="f64"), T, cu(np.zeros(8)), s64,
+                                     cu(xi), cu(u), want_jac=False)
+    np.testing.assert_array_equal(npy(a64).astype(bool), acc)
