@@ -140,6 +140,24 @@ __device__ __forceinline__ void warp_arrive(uint32_t bar) {
 template <int P>
 using PassC = std::integral_constant<int, P>;
 
+// hi + lo += v without rounding loss (Knuth's two-sum; the error term is carried in lo)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+}
+
+// ln(p) for p >= 1: the binary exponent is taken exactly and only the mantissa in [1, 2) goes
+// through the hardware log2 (absolute error about 2^-22 there)
+__device__ __forceinline__ float log_of_product(float p) {
+    const int b = __float_as_int(p);
+    const float e = (float)((b >> 23) - 127);
+    const float mant = __int_as_float((b & 0x007fffff) | 0x3f800000);
+    return (e + __log2f(mant)) * 0.69314718055994531f;
+}
+
 template <typename S_>
 __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A) {
     if (A.skip && *(volatile const int *)A.skip) return;
@@ -298,7 +316,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         };
         float xt[kCols];              // the proposal (own dimensions)
         float gs[kCols];              // running G sum (own dimensions)
-        double ll0 = 0.0, ll1 = 0.0;  // log-likelihood partials (own columns) of the two passes
+        // -sum softplus partials (own columns) of the two passes, compensated (hi + lo)
+        float ll0h = 0.0f, ll0l = 0.0f, ll1h = 0.0f, ll1l = 0.0f;
         bool ok = true;
 #pragma unroll
         for (int i = 0; i < kCols; i++) xt[i] = gs[i] = 0.0f;
@@ -363,35 +382,33 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 const float4 ya = ys4[0], yb = ys4[1];
                 const float yv8[kCols] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
                 float chi[kCols], clo[kCols], whi[kCols];
-                float llc = 0.0f;
-                const int nbase = j * kNB + d0;
-                const bool full = nbase + kCols <= N;
+                // The log-likelihood enters the MH ratio only as ll(x~) - ll(x), so its part
+                // sum_n y_n z_n is taken in the tail as (x~ - x) . X^T y, and here only
+                // -sum_n softplus(z_n) = -sum_n max(z_n, 0) - log prod_n (1 + e^-|z_n|).  Padded
+                // rows (n >= N) have X_n = 0, hence z = 0, c X_n = 0 and w X_n.X_n = 0, and a
+                // log 2 that is the same in both passes: no masking is needed.
+                float negrelu = 0.0f, prod = 1.0f;
 #pragma unroll
                 for (int i = 0; i < kCols; i++) {
                     const float zz = zcur[i];
-                    const float yv = yv8[i];
                     const float m = __expf(-fabsf(zz));
-                    const float qv = __fdividef(1.0f, 1.0f + m);
+                    const float onep = 1.0f + m;
+                    const float qv = __fdividef(1.0f, onep);
                     const float mq = m * qv;
-                    const float p = zz >= 0.0f ? qv : mq;   // sigmoid(z)
-                    const float pc = zz >= 0.0f ? mq : qv;  // 1 - sigmoid(z)
-                    float c = yv - p;
-                    float w = kW ? p * pc : 0.0f;
-                    float ln = yv * zz - (fmaxf(zz, 0.0f) + __logf(1.0f + m));  // y z - softplus(z)
-                    if (!full && nbase + i >= N) {
-                        c = 0.0f;
-                        w = 0.0f;
-                        ln = 0.0f;
-                    }
-                    llc += ln;
+                    const bool pos = zz >= 0.0f;
+                    const float p = pos ? qv : mq;   // sigmoid(z)
+                    const float c = yv8[i] - p;
+                    negrelu -= fmaxf(zz, 0.0f);
+                    prod *= onep;
                     // c = c_hi + c_lo exactly; the tensor core drops the low 13 bits of c_lo
                     // (below 2^-20 |c|) and of w
                     chi[i] = tf32_trunc(c);
                     clo[i] = c - chi[i];
-                    if (kW) whi[i] = w;
+                    if (kW) whi[i] = p * (pos ? mq : qv);  // sigmoid'(z)
                 }
-                if (pass) ll1 += (double)llc;
-                else ll0 += (double)llc;
+                const float llc = negrelu - log_of_product(prod);
+                if (pass) two_sum_acc(ll1h, ll1l, llc);
+                else two_sum_acc(ll0h, ll0l, llc);
                 unsigned char *cw = sm + oCW + b * kCWStride;
 #pragma unroll
                 for (int c4 = 0; c4 < 2; c4++) {
@@ -449,11 +466,16 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         // tail (x = s_{t-1}, the noise, s_t) is issued before any of them is used.
         double *part = reinterpret_cast<double *>(sm + oPart);
         int *accf = reinterpret_cast<int *>(sm + oAcc);
-        float x[kCols], xv[kCols], sv[kCols];
+        float x[kCols], xv[kCols], sv[kCols], ty[kCols];
         load_x(x);
         load_xi(xv);
+        const float *xty = reinterpret_cast<const float *>(static_cast<const unsigned char *>(A.tc_img) +
+                                                           (size_t)nch * kImg);
 #pragma unroll
-        for (int i = 0; i < kCols; i++) sv[i] = (tv && d0 + i < D) ? s[(size_t)t * D + d0 + i] : 0.0f;
+        for (int i = 0; i < kCols; i++) {
+            sv[i] = (tv && d0 + i < D) ? s[(size_t)t * D + d0 + i] : 0.0f;
+            ty[i] = xty[d0 + i];
+        }
         {
             const float inv2sp2 = 0.5f * inv_sp2, inv4e = 0.25f / eps;
             float qf = 0.0f;
@@ -462,10 +484,11 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 if (d0 + i < D) {
                     const float g2 = gs[i] - xt[i] * inv_sp2;
                     const float e = x[i] - xt[i] - eps * g2;
-                    qf += -(xt[i] - x[i]) * (xt[i] + x[i]) * inv2sp2 - e * e * inv4e + 0.5f * xv[i] * xv[i];
+                    qf += (xt[i] - x[i]) * ty[i] - (xt[i] - x[i]) * (xt[i] + x[i]) * inv2sp2 -
+                          e * e * inv4e + 0.5f * xv[i] * xv[i];
                 }
             }
-            part[h * kM + r] = (ll1 - ll0) + (double)qf;
+            part[h * kM + r] = (((double)ll1h - (double)ll0h) + ((double)ll1l - (double)ll0l)) + (double)qf;
         }
         named_bar(1, kEpiThreads);
         const bool valid = tv && ok && !*abort_f;
@@ -486,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             accf[r] = acc;
         }
         named_bar(1, kEpiThreads);
-        double err = -INFINITY, rmax = 0.0;
+        float err = -INFINITY, rmax = 0.0f;
         float dh[kCols];
 #pragma unroll
         for (int i = 0; i < kCols; i++) dh[i] = 0.0f;
@@ -496,6 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             tmem_ld8(lrow + kColH + (uint32_t)d0, dh);
             tmem_wait_ld();
         }
+        const float rtolf = (float)A.rtol;
         if (valid) {
             const bool acc = accf[r] != 0;
             S_ *bout = static_cast<S_ *>(A.b_out);
@@ -509,10 +533,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     const size_t o = (size_t)t * D + d;
                     const float f = acc ? xt[i] : x[i];
                     const float rr = f - sv[i];
-                    const double ar = fabs((double)rr);
-                    const double ee = ar - A.rtol * fabs((double)sv[i]);
-                    err = isnan(ee) ? INFINITY : fmax(err, ee);
-                    rmax = isnan(ar) ? INFINITY : fmax(rmax, ar);
+                    const float ar = fabsf(rr);
+                    const float ee = ar - rtolf * fabsf(sv[i]);
+                    err = isnan(ee) ? INFINITY : fmaxf(err, ee);
+                    rmax = isnan(ar) ? INFINITY : fmaxf(rmax, ar);
                     if (bout) store_as<S_, float>(bout + o, rr);
                     if (fout) fout[o] = f;
                     if (aout) {
@@ -524,28 +548,31 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             }
         }
         if (A.stats) {
-            double *red = reinterpret_cast<double *>(sm + oRed);
-            const double e1 = warp_max(err), e2 = warp_max(rmax), e3 = warp_min(margin);
-            const double e4 = warp_sum((double)acc_i);
+            // residuals and margins are reduced as FP32 (the residual is an FP32 quantity; the
+            // margin is a diagnostic), decisions as integers
+            float *red = reinterpret_cast<float *>(sm + oRed);
+            const float e1 = warp_max(err), e2 = warp_max(rmax), e3 = warp_min((float)margin);
+            const int e4 = __reduce_add_sync(0xffffffffu, acc_i);
             if (lane == 0) {
                 red[4 * warp + 0] = e1;
                 red[4 * warp + 1] = e2;
                 red[4 * warp + 2] = e3;
-                red[4 * warp + 3] = e4;
+                reinterpret_cast<int *>(red)[4 * warp + 3] = e4;
             }
             named_bar(1, kEpiThreads);
             if (tid == 0) {
-                double m1 = red[0], m2 = red[1], m3 = red[2], m4 = red[3];
+                float m1 = red[0], m2 = red[1], m3 = red[2];
+                int m4 = reinterpret_cast<int *>(red)[3];
                 for (int w = 1; w < kEpiWarps; w++) {
-                    m1 = fmax(m1, red[4 * w]);
-                    m2 = fmax(m2, red[4 * w + 1]);
-                    m3 = fmin(m3, red[4 * w + 2]);
-                    m4 += red[4 * w + 3];
+                    m1 = fmaxf(m1, red[4 * w]);
+                    m2 = fmaxf(m2, red[4 * w + 1]);
+                    m3 = fminf(m3, red[4 * w + 2]);
+                    m4 += reinterpret_cast<int *>(red)[4 * w + 3];
                 }
-                atomic_max_d(&A.stats->err, m1);
-                atomic_max_d(&A.stats->rmax, m2);
-                atomic_min_d(&A.stats->min_margin, m3);
-                if (m4 > 0) atomicAdd(&A.stats->accepts, (unsigned long long)(m4 + 0.5));
+                atomic_max_d(&A.stats->err, (double)m1);
+                atomic_max_d(&A.stats->rmax, (double)m2);
+                atomic_min_d(&A.stats->min_margin, (double)m3);
+                if (m4 > 0) atomicAdd(&A.stats->accepts, (unsigned long long)m4);
             }
         }
     }
@@ -590,13 +617,36 @@ bool logreg_tc_supported(const EvalArgs &A) {
            (A.jac == PMCMC_JAC_ZERO || (A.jac == PMCMC_JAC_DIAG && A.gate_grad == 0));
 }
 
-size_t logreg_tc_image_bytes(int N) { return (size_t)ceil_div(N, kNB) * kImg; }
+// the chunk images, then X^T y (kDP floats)
+size_t logreg_tc_image_bytes(int N) { return (size_t)ceil_div(N, kNB) * kImg + kDP * sizeof(float); }
+
+// X^T y (FP64 sums, rounded once), after the chunk images; padded dimensions are zero
+__global__ void logreg_tc_xty_kernel(const float *__restrict__ X, const float *__restrict__ y, int N, int D,
+                                     float *__restrict__ xty) {
+    __shared__ double part[256];
+    for (int d = 0; d < kDP; d++) {
+        double acc = 0.0;
+        if (d < D)
+            for (int n = threadIdx.x; n < N; n += blockDim.x) acc += (double)y[n] * (double)X[(size_t)n * D + d];
+        part[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) xty[d] = (float)part[0];
+        __syncthreads();
+    }
+}
 
 cudaError_t launch_logreg_tc_pack(const void *X, const void *y, int N, int D, void *img, cudaStream_t st) {
     if (N <= 0 || D > kDP) return cudaErrorInvalidValue;
     logreg_tc_pack_kernel<<<ceil_div(N, kNB), 256, 0, st>>>(static_cast<const float *>(X),
                                                            static_cast<const float *>(y), N, D,
                                                            static_cast<unsigned char *>(img));
+    logreg_tc_xty_kernel<<<1, 256, 0, st>>>(static_cast<const float *>(X), static_cast<const float *>(y), N, D,
+                                            reinterpret_cast<float *>(static_cast<unsigned char *>(img) +
+                                                                      (size_t)ceil_div(N, kNB) * kImg));
     return cudaGetLastError();
 }
 

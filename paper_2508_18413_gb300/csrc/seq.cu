@@ -42,7 +42,9 @@ struct SeqCtx {
 constexpr int kRed = 0;        // 32 per-warp partials of a block sum
 constexpr int kDslot = 32;     // 2 cluster-exchange slots of the partial log-likelihood
 constexpr int kFlag = 38;      // decision word (as a double slot)
-constexpr int kNDouble = 40;
+constexpr int kLogu = 40;      // log u of the next kLogBlock steps
+constexpr int kLogBlock = 256;
+constexpr int kNDouble = kLogu + kLogBlock;
 
 template <typename R>
 struct SeqMem {
@@ -105,25 +107,70 @@ __device__ __forceinline__ void sum2(double a, double b, double *dbl, int D, dou
     __syncthreads();  // the partials may be overwritten afterwards
 }
 
+// Sum of a per-thread value over the CTA, returned to thread 0 only.  Double arithmetic is on
+// GB300's narrow FP64 pipe (1/64 of the FP32 rate), so an FP32 value is summed as a compensated
+// (hi, lo) pair (two-sum per step, exact up to the lo rounding) and only the per-warp pairs are
+// added in FP64; a double value is summed in FP64.
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
+}
+__device__ __forceinline__ void warp_pair_sum(float &hi, float &lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        two_sum(hi, lo, h2);
+        lo += l2;
+    }
+}
+// exp(-|z|), 1 / (1 + e) and log(1 + e) for e in (0, 1]: hardware approximations in FP32 (as the
+// parallel evaluate kernels use), library functions in FP64
+__device__ __forceinline__ double exp_neg_abs(double z) { return exp(-fabs(z)); }
+__device__ __forceinline__ float exp_neg_abs(float z) { return __expf(-fabsf(z)); }
+__device__ __forceinline__ double recip1p(double e) { return 1.0 / (1.0 + e); }
+__device__ __forceinline__ float recip1p(float e) { return __fdividef(1.0f, 1.0f + e); }
+__device__ __forceinline__ double log1p_unit(double e) { return log1p(e); }
+__device__ __forceinline__ float log1p_unit(float e) { return __logf(1.0f + e); }
+
+template <typename R>
+struct LLAcc {  // per-thread accumulator of log-likelihood terms
+    double d = 0.0;
+    __device__ __forceinline__ void add(R v) { d += (double)v; }
+    __device__ __forceinline__ void to_warp_slot(double *slot) {
+        d = warp_sum(d);
+        if ((threadIdx.x & 31) == 0) *slot = d;
+    }
+};
+template <>
+struct LLAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v) { two_sum(hi, lo, v); }
+    __device__ __forceinline__ void to_warp_slot(double *slot) {
+        warp_pair_sum(hi, lo);
+        if ((threadIdx.x & 31) == 0) *slot = (double)hi + (double)lo;
+    }
+};
+
 // Logistic regression: likelihood gradient X^T (y - sigmoid(X v)) into out[0..D) (every CTA of
 // the chain gets the full sum) and the log-likelihood sum_n y z - softplus(z) as the return value.
 template <typename R>
 __device__ double pass_logreg(const SeqCtx &c, const SeqMem<R> &m, const R *v, R *out, int buf) {
     const int tid = threadIdx.x, nt = blockDim.x, D = c.D;
-    double llp = 0.0;
+    LLAcc<R> llp;
     for (int n = tid; n < c.rows; n += nt) {
         const R *xr = m.Xs + (size_t)n * c.Dp;
         R z = R(0);
         for (int d = 0; d < D; d++) z = fma(xr[d], v[d], z);
-        const R e = exp(-fabs(z));
-        const R q = R(1) / (R(1) + e);
+        const R e = exp_neg_abs(z);
+        const R q = recip1p(e);
         const R p = z >= R(0) ? q : e * q;  // sigmoid(z)
         const R yv = m.ys[n];
         m.cw[n] = yv - p;
-        llp += (double)(yv * z - (fmax(z, R(0)) + log1p(e)));
+        llp.add(yv * z - (fmax(z, R(0)) + log1p_unit(e)));
     }
-    llp = warp_sum(llp);
-    if ((tid & 31) == 0) m.dbl[kRed + (tid >> 5)] = llp;
+    llp.to_warp_slot(m.dbl + kRed + (tid >> 5));
     __syncthreads();
     for (int e = tid; e < c.K * D; e += nt) {
         const int k = e / D, d = e - k * D;
@@ -245,17 +292,18 @@ __device__ void run_chain(const SeqChain &ch, int cs, int rank, unsigned char *r
     R *sout = static_cast<R *>(ch.s_out);
     const bool writer = rank == 0;
     R xi_cur = tid < D ? xin[tid] : R(0);
-    double u_cur = tid == 0 ? ch.u[0] : 0.0;
     const R sq = sqrt(R(2) * eps);
 
     for (int t = 0; t < c.T; t++) {
+        // log u of the next kLogBlock steps, one per thread, off the per-step critical path
+        if ((t % kLogBlock) == 0) {
+            for (int i = tid; i < kLogBlock; i += nt)
+                m.dbl[kLogu + i] = t + i < c.T ? log(ch.u[t + i]) : 0.0;
+            __syncthreads();
+        }
         // prefetch the next step's noise
         R xi_nxt = R(0);
-        double u_nxt = 0.0;
-        if (t + 1 < c.T) {
-            if (tid < D) xi_nxt = xin[(size_t)(t + 1) * D + tid];
-            if (tid == 0) u_nxt = ch.u[t + 1];
-        }
+        if (t + 1 < c.T && tid < D) xi_nxt = xin[(size_t)(t + 1) * D + tid];
         double gap = 0.0;  // log alpha-type quantity compared with log u: ell (MALA) or H0 - HL (HMC)
         double lpt = 0.0;  // log p at the proposal
         if (c.sampler == PMCMC_MALA) {
@@ -324,7 +372,7 @@ __device__ void run_chain(const SeqChain &ch, int cs, int rank, unsigned char *r
         }
         if (tid == 0) {
             const double la = (gap < 0.0 || isnan(gap)) ? gap : 0.0;
-            m.dbl[kFlag] = (la - log(u_cur) > 0.0) ? 1.0 : 0.0;
+            m.dbl[kFlag] = (la - m.dbl[kLogu + t % kLogBlock] > 0.0) ? 1.0 : 0.0;
         }
         __syncthreads();
         const bool acc = m.dbl[kFlag] != 0.0;
@@ -340,7 +388,6 @@ __device__ void run_chain(const SeqChain &ch, int cs, int rank, unsigned char *r
             if (tid == 0 && ch.acc_out) ch.acc_out[t] = acc ? 1 : 0;
         }
         xi_cur = xi_nxt;
-        u_cur = u_nxt;
         __syncthreads();  // x and g settled before the next proposal reads them
     }
     chain_sync(cs);  // no CTA leaves while another may still read its shared memory
