@@ -68,9 +68,19 @@ def tensor_peak_fp32_equiv():
     return bf16 * (1.1 / 2.25) / 3.0, src
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
-# kernel, eval_logreg_tc_kernel, from an ncu capture of the current kernel on this workload.
-EVAL_TRAFFIC_BYTES = 4159744
+def eval_traffic_bytes():
+    """DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
+    kernel, taken from the committed record of its last ncu capture; None when the kernel source
+    has changed since (the record carries a hash of the source it was captured from)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_counters.json")))["eval_logreg_tc_kernel"]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    except Exception:
+        return None
 
 
 def parse():
@@ -696,7 +706,7 @@ def run_ours(args):
                      "kernel": ("eval_logreg_tc_kernel (evaluate and linearise, tcgen05 3xTF32)"
                                 if tc else "eval_logreg_kernel (evaluate and linearise)"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": EVAL_TRAFFIC_BYTES if tc else None,
+                     "frac": achieved / peak, "traffic": eval_traffic_bytes() if tc else None,
                      "peak_source": peak_src + (" x 1.1/2.25 (tf32) / 3 (three products)" if tc else ""),
                      "achieved_is": "algorithmic FP32 flops (10 N D per timestep) / launch time",
                      "avg_launch_ms": avg_eval_ms, "launches": prof["eval_launches"],
