@@ -363,15 +363,15 @@ def run_configs(P, torch, dev, flush, stream):
     sopt = P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, precision="f32")
     sms, (sq, _) = _time_fn(lambda: P.pmcmc_seq_solve(tgt, sopt, c.T, s0, xid, ud), 2, 1, flush, stream, torch)
     keep["c3_seq32"] = sq.cpu().numpy()
-    for name, opt in (("c3_diag", P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, jac="diag", clip=1,
+    for name, opt in (("c3_diag", P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, jac="diag", clip=0,
                                             precision="f32", atol=1e-6, rtol=1e-6)),
-                      ("c3_bf16", P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, jac="diag", clip=1,
+                      ("c3_bf16", P.Options(sampler="hmc", step=c.step, leapfrog_L=c.L, jac="diag", clip=0,
                                             precision="f32_scan_bf16", atol=1e-6, rtol=1e-6)),
                       ("c3_block", P.Options(sampler="hmc_par_leapfrog", step=c.step, leapfrog_L=c.L,
                                              jac="block2", precision="f32", atol=1e-6, rtol=1e-6))):
         ms, (s, res) = _time_fn(lambda: P.pmcmc_solve(tgt, opt, c.T, s0, xi=xid, u=ud), 2, 1, flush, stream, torch)
         entry(name, c.T, ms, res, sms, {"workload": f"{c.name}: HMC banana L={c.L} step {c.step}, {opt.jac}, "
-                                                    f"{opt.precision}, atol/rtol 1e-6",
+                                                    f"clip {opt.clip}, {opt.precision}, atol/rtol 1e-6",
                                          "accept_rate": res["accept_rate"]})
         keep[name] = s.cpu().numpy()
 

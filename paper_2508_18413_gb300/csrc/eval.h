@@ -8,6 +8,7 @@
 namespace pm {
 
 struct EvalStats;
+struct ScanCtl;
 
 struct EvalArgs {
     // problem
@@ -53,6 +54,14 @@ struct EvalArgs {
     const void *tc_img = nullptr;     // chunk images of the design (launch_logreg_tc_pack)
     unsigned int *timeout = nullptr;  // set to 1 when a bounded wait ran out
     unsigned int spin_limit = 0;      // polls per wait; 0 = default
+    // Newton update fused into the tensor-core evaluate kernel (fs_flags non-null): the kernel
+    // also solves delta_t = J_t delta_{t-1} + r_t (carry from the published aggregates of the
+    // earlier tiles) and writes s + delta to the other iterate buffer.  The parity of *iter
+    // picks the buffers: even reads s and writes s_alt, odd the reverse.
+    void *s_alt = nullptr;
+    unsigned int *fs_flags = nullptr;  // one per 128-timestep tile, epoch-tagged
+    float *fs_agg = nullptr;           // tiles x 2 x 32: tile aggregates (A, B)
+    ScanCtl *fs_ctl = nullptr;         // ticket, done, epoch, timeout
 };
 
 cudaError_t launch_eval_small(const EvalArgs &A, cudaStream_t st);
@@ -71,5 +80,6 @@ bool logreg_tc_supported(const EvalArgs &A);
 size_t logreg_tc_image_bytes(int N);
 cudaError_t launch_logreg_tc_pack(const void *X, const void *y, int N, int D, void *img, cudaStream_t st);
 cudaError_t launch_eval_logreg_tc(const EvalArgs &A, cudaStream_t st);
+constexpr int kTcTileT = 128;  // timesteps per CTA of the tensor-core evaluate kernel
 
 }  // namespace pm

@@ -37,6 +37,7 @@
 #include "common.cuh"
 #include "eval.h"
 #include "internal.h"
+#include "lookback.cuh"
 #include "tc.cuh"
 
 namespace pm {
@@ -93,7 +94,14 @@ constexpr int oPart = oMisc + 16;              // double [4][128]: per-warpgroup
 constexpr int oAcc = oPart + kGroups * kM * 8; // int [128]: decisions
 constexpr int oRed = oAcc + kM * 4;            // double [16][4]: per-warp statistics
 constexpr int oLogu = oRed + kEpiWarps * 4 * 8; // double [128]: log u of each timestep
-constexpr int kSmemUsed = oLogu + kM * 8;
+// fused Newton update: per-warp scan totals [16 warps][8 channels][A, B], the carries into the
+// four warps of a warpgroup [4][32] (A and B), the 16 segment compositions of the earlier tiles'
+// aggregates, the tile carry [32]
+constexpr int oFw = oLogu + kM * 8;
+constexpr int oFpre = oFw + kEpiWarps * 8 * 2 * 4;
+constexpr int oFseg = oFpre + 4 * 32 * 2 * 4;      // [16][32] (A, B): segment compositions
+constexpr int oFcar = oFseg + kEpiWarps * 32 * 2 * 4;
+constexpr int kSmemUsed = oFcar + 32 * 4;
 constexpr int kSmemBytes = kSmemUsed + 1024;   // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 static_assert(oStage % 1024 == 0 && kStageStride % 1024 == 0 && oCW % 1024 == 0, "alignment");
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
     const uint32_t sb = smem_u32(sm);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int T = A.T, D = A.D, N = A.N;
-    const int t0 = blockIdx.x * kM;
+    const bool fused = A.fs_flags != nullptr;
     const int nch = (N + kNB - 1) / kNB;
     const bool want_dh = A.jac == PMCMC_JAC_DIAG;
     const unsigned int limit = A.spin_limit ? A.spin_limit : kDefaultSpinLimit;
@@ -183,6 +191,15 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             mbar_init(bar(i), cnt);
         }
         *abort_f = 0;
+        // the fused Newton update walks back over earlier tiles: tiles are taken by ticket, in
+        // dispatch order, so every tile a CTA waits on belongs to a CTA already running
+        unsigned int tile_ = blockIdx.x, ep = 0;
+        if (fused) {
+            tile_ = atomicAdd(&A.fs_ctl->ticket, 1u);
+            ep = *(volatile unsigned int *)&A.fs_ctl->epoch;
+        }
+        reinterpret_cast<unsigned int *>(sm + oMisc)[2] = tile_;
+        reinterpret_cast<unsigned int *>(sm + oMisc)[3] = ep;
         fence_barrier_init();
     }
     if (warp == kMmaWarp) {
@@ -193,6 +210,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = *tmem_slot;
+    const int tile = (int)reinterpret_cast<const unsigned int *>(sm + oMisc)[2];
+    const unsigned int epoch = reinterpret_cast<const unsigned int *>(sm + oMisc)[3];
+    const int t0 = tile * kM;
 
     if (warp == kCopyWarp && lane == kCopyLane) {
         // ---------------- producer: chunk images, both passes ----------------
@@ -296,7 +316,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         const uint32_t lrow = tm + ((uint32_t)(q * 32) << 16);
         const float eps = (float)A.eps;
         const float inv_sp2 = (float)(1.0 / (A.sigma_p * A.sigma_p));
-        const float *s = static_cast<const float *>(A.s);
+        // fused mode: the iterate ping-pongs between A.s and A.s_alt with the iteration parity
+        const int par = (fused && A.iter) ? (*A.iter & 1) : 0;
+        const float *s = static_cast<const float *>(par ? A.s_alt : A.s);
+        float *s_next = static_cast<float *>(par ? const_cast<void *>(A.s) : A.s_alt);
         const float *s0 = static_cast<const float *>(A.s0);
         const float *xin = static_cast<const float *>(A.xi);
         // own dimensions of x = s_{t-1} and of the noise, re-read where needed (L2)
@@ -316,17 +339,18 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         };
         float xt[kCols];              // the proposal (own dimensions)
         float gs[kCols];              // running G sum (own dimensions)
+        // own dimensions of x = s_{t-1}, the noise, s_t and X^T y (loaded at each pass end)
+        float x[kCols], xv[kCols], sv[kCols], ty[kCols];
+        const float *xty = reinterpret_cast<const float *>(static_cast<const unsigned char *>(A.tc_img) +
+                                                           (size_t)nch * kImg);
         // -sum softplus partials (own columns) of the two passes, compensated (hi + lo)
         float ll0h = 0.0f, ll0l = 0.0f, ll1h = 0.0f, ll1l = 0.0f;
         bool ok = true;
 #pragma unroll
         for (int i = 0; i < kCols; i++) xt[i] = gs[i] = 0.0f;
-        {
-            float x[kCols];
-            load_x(x);
-            put_row_pair(sm + oVhi, sm + oVlo, r, h, x);
-            warp_arrive(bar(bVready));
-        }
+        load_x(x);
+        put_row_pair(sm + oVhi, sm + oVlo, r, h, x);
+        warp_arrive(bar(bVready));
         // log u (FP64) while the first products run; read back by the same thread at the end
         if (h == 0) reinterpret_cast<double *>(sm + oLogu)[r] = tv ? log(A.u[t]) : 0.0;
         auto add_partial = [&](int kc) {  // G of chunk kc, own dimensions
@@ -432,7 +456,18 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 }
                 warp_arrive(bar(bCfull + (k & 3)));
             }
-            // pass end: the last one or two partials complete G of this pass
+            // pass end: the last one or two partials complete G of this pass.  The global loads
+            // the pass end and the tail need (x, the noise; s_t and X^T y after pass 2) are issued
+            // before the wait, so their latency overlaps the last products.
+            load_x(x);
+            load_xi(xv);
+            if (pass == 1) {
+#pragma unroll
+                for (int i = 0; i < kCols; i++) {
+                    sv[i] = (tv && d0 + i < D) ? s[(size_t)t * D + d0 + i] : 0.0f;
+                    ty[i] = xty[d0 + i];
+                }
+            }
             if (ok && (ok = warp_wait(bar(bGdone), (uint32_t)pass, abort_f, limit))) {
                 tc_fence_after();
                 const int kb = pass * nch;
@@ -440,9 +475,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 add_partial(kb + nch - 1);
                 if (pass == 0) {
                     // the proposal x~ = x + eps grad log p(x) + sqrt(2 eps) xi (own dimensions)
-                    float x[kCols], xv[kCols];
-                    load_x(x);
-                    load_xi(xv);
                     const float sq = sqrtf(2.0f * eps);
 #pragma unroll
                     for (int i = 0; i < kCols; i++)
@@ -466,16 +498,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         // tail (x = s_{t-1}, the noise, s_t) is issued before any of them is used.
         double *part = reinterpret_cast<double *>(sm + oPart);
         int *accf = reinterpret_cast<int *>(sm + oAcc);
-        float x[kCols], xv[kCols], sv[kCols], ty[kCols];
-        load_x(x);
-        load_xi(xv);
-        const float *xty = reinterpret_cast<const float *>(static_cast<const unsigned char *>(A.tc_img) +
-                                                           (size_t)nch * kImg);
-#pragma unroll
-        for (int i = 0; i < kCols; i++) {
-            sv[i] = (tv && d0 + i < D) ? s[(size_t)t * D + d0 + i] : 0.0f;
-            ty[i] = xty[d0 + i];
-        }
         {
             const float inv2sp2 = 0.5f * inv_sp2, inv4e = 0.25f / eps;
             float qf = 0.0f;
@@ -520,6 +542,12 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             tmem_wait_ld();
         }
         const float rtolf = (float)A.rtol;
+        float fa[kCols], fb[kCols];  // the scan pair (J_t, r_t) of each own dimension; identity if unused
+#pragma unroll
+        for (int i = 0; i < kCols; i++) {
+            fa[i] = 1.0f;
+            fb[i] = 0.0f;
+        }
         if (valid) {
             const bool acc = accf[r] != 0;
             S_ *bout = static_cast<S_ *>(A.b_out);
@@ -537,42 +565,178 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     const float ee = ar - rtolf * fabsf(sv[i]);
                     err = isnan(ee) ? INFINITY : fmaxf(err, ee);
                     rmax = isnan(ar) ? INFINITY : fmaxf(rmax, ar);
+                    float jv = 0.0f;
+                    if (want_dh) jv = post_jac(acc ? 1.0f + eps * (-dh[i] - inv_sp2) : 1.0f, damping, A.clip);
                     if (bout) store_as<S_, float>(bout + o, rr);
                     if (fout) fout[o] = f;
-                    if (aout) {
-                        float jv = 0.0f;
-                        if (want_dh) jv = post_jac(acc ? 1.0f + eps * (-dh[i] - inv_sp2) : 1.0f, damping, A.clip);
-                        store_as<S_, float>(aout + o, jv);
+                    if (aout) store_as<S_, float>(aout + o, jv);
+                    fa[i] = jv;
+                    fb[i] = rr;
+                }
+            }
+        }
+        float dmx = 0.0f;        // fused update: max |delta| and non-finite resets of own elements
+        unsigned int nres = 0;
+        if (fused) {
+            // Newton update of this tile (Eq. 3 in delta form): delta_t = J_t delta_{t-1} + r_t
+            // over the 128 timesteps, carried in from the earlier tiles, and s_t + delta_t
+            // written to the other iterate buffer.  Lanes are timesteps, so a warp scans its 32
+            // timesteps of 8 channels with shuffles; warp totals compose across the four warps
+            // of a warpgroup into the tile aggregate, which is published.  The carry into the tile
+            // composes the aggregates of all earlier tiles (published independently of any
+            // carry, so no tile waits on another's carry): warp w composes a segment of them,
+            // warp 0 folds the 16 segments.
+            float *wtot = reinterpret_cast<float *>(sm + oFw);    // [warp][channel][A, B]
+            float *pre = reinterpret_cast<float *>(sm + oFpre);   // [q][32] A, then [q][32] B
+            float *segm = reinterpret_cast<float *>(sm + oFseg);  // [16 segments][32][A, B]
+            float *car = reinterpret_cast<float *>(sm + oFcar);   // [32]
+            float IA[kCols], IB[kCols];
+#pragma unroll
+            for (int i = 0; i < kCols; i++) {
+                IA[i] = fa[i];
+                IB[i] = fb[i];
+            }
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                for (int i = 0; i < kCols; i++) {
+                    const float pa = __shfl_up_sync(0xffffffffu, IA[i], off);
+                    const float pb = __shfl_up_sync(0xffffffffu, IB[i], off);
+                    if (lane >= off) {
+                        IB[i] = IA[i] * pb + IB[i];
+                        IA[i] = IA[i] * pa;
                     }
+                }
+            }
+            if (lane == 31) {
+#pragma unroll
+                for (int i = 0; i < kCols; i++) {
+                    wtot[(warp * kCols + i) * 2] = IA[i];
+                    wtot[(warp * kCols + i) * 2 + 1] = IB[i];
+                }
+            }
+            named_bar(1, kEpiThreads);
+            if (tid < kDP) {  // channel tid = 8 h' + i': compose warps 4 h' .. 4 h' + 3
+                const int hh = tid >> 3, ii = tid & 7;
+                float PA = 1.0f, PB = 0.0f;
+#pragma unroll
+                for (int qq = 0; qq < 4; qq++) {
+                    pre[qq * 32 + tid] = PA;
+                    pre[128 + qq * 32 + tid] = PB;
+                    const float WA = wtot[((4 * hh + qq) * kCols + ii) * 2];
+                    const float WB = wtot[((4 * hh + qq) * kCols + ii) * 2 + 1];
+                    PB = WA * PB + WB;
+                    PA = WA * PA;
+                }
+                A.fs_agg[((size_t)tile * 2) * kDP + tid] = PA;
+                A.fs_agg[((size_t)tile * 2 + 1) * kDP + tid] = PB;
+                __threadfence();
+            }
+            __syncwarp();
+            if (tid == 0) st_release(A.fs_flags + tile, make_flag(epoch, kFlagAgg));
+            // segment of warp w: tiles [w per, (w + 1) per) below this tile; lane = channel
+            {
+                const int per = (tile + kEpiWarps - 1) / kEpiWarps;
+                const int j0 = warp * per, j1 = min(tile, j0 + per);
+                float SA = 1.0f, SB = 0.0f;
+                for (int jb = j0; jb < j1; jb += 32) {
+                    const int nj = min(32, j1 - jb);
+                    if (lane < nj) wait_flag(A.fs_flags, jb + lane, epoch, limit, A.fs_ctl);
+                    __syncwarp();
+                    for (int jc = 0; jc < nj; jc += 8) {
+                        float ga[8], gb[8];
+#pragma unroll
+                        for (int u = 0; u < 8; u++) {
+                            const int j = jb + jc + u;
+                            const bool on = jc + u < nj;
+                            ga[u] = on ? __ldcg(A.fs_agg + ((size_t)j * 2) * kDP + lane) : 1.0f;
+                            gb[u] = on ? __ldcg(A.fs_agg + ((size_t)j * 2 + 1) * kDP + lane) : 0.0f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; u++) {  // later tiles on the left
+                            SB = ga[u] * SB + gb[u];
+                            SA = ga[u] * SA;
+                        }
+                    }
+                }
+                segm[(warp * 32 + lane) * 2] = SA;
+                segm[(warp * 32 + lane) * 2 + 1] = SB;
+            }
+            named_bar(1, kEpiThreads);
+            if (warp == 0) {
+                float c = 0.0f;  // the carry into tile 0 is zero
+#pragma unroll
+                for (int w = 0; w < kEpiWarps; w++)
+                    c = segm[(w * 32 + lane) * 2] * c + segm[(w * 32 + lane) * 2 + 1];
+                car[lane] = c;
+            }
+            named_bar(1, kEpiThreads);
+#pragma unroll
+            for (int i = 0; i < kCols; i++) {
+                const int d = d0 + i;
+                const float cq = pre[q * 32 + d] * car[d] + pre[128 + q * 32 + d];  // delta before warp q
+                const float dl = IA[i] * cq + IB[i];
+                if (valid && d < D) {
+                    float sn = sv[i] + dl;
+                    if (!isfinite(sn)) {
+                        sn = s0[d];
+                        nres++;
+                    } else {
+                        dmx = fmaxf(dmx, fabsf(dl));
+                    }
+                    s_next[(size_t)t * D + d] = sn;
                 }
             }
         }
         if (A.stats) {
-            // residuals and margins are reduced as FP32 (the residual is an FP32 quantity; the
-            // margin is a diagnostic), decisions as integers
+            // residuals, margins and update sizes are reduced as FP32 (the residual is an FP32
+            // quantity; the margin is a diagnostic), decisions and resets as integers
             float *red = reinterpret_cast<float *>(sm + oRed);
             const float e1 = warp_max(err), e2 = warp_max(rmax), e3 = warp_min((float)margin);
             const int e4 = __reduce_add_sync(0xffffffffu, acc_i);
+            const float e5 = warp_max(dmx);
+            const unsigned int e6 = __reduce_add_sync(0xffffffffu, nres);
             if (lane == 0) {
-                red[4 * warp + 0] = e1;
-                red[4 * warp + 1] = e2;
-                red[4 * warp + 2] = e3;
-                reinterpret_cast<int *>(red)[4 * warp + 3] = e4;
+                red[8 * warp + 0] = e1;
+                red[8 * warp + 1] = e2;
+                red[8 * warp + 2] = e3;
+                reinterpret_cast<int *>(red)[8 * warp + 3] = e4;
+                red[8 * warp + 4] = e5;
+                reinterpret_cast<unsigned int *>(red)[8 * warp + 5] = e6;
             }
             named_bar(1, kEpiThreads);
             if (tid == 0) {
-                float m1 = red[0], m2 = red[1], m3 = red[2];
+                float m1 = red[0], m2 = red[1], m3 = red[2], m5 = red[4];
                 int m4 = reinterpret_cast<int *>(red)[3];
+                unsigned int m6 = reinterpret_cast<unsigned int *>(red)[5];
                 for (int w = 1; w < kEpiWarps; w++) {
-                    m1 = fmaxf(m1, red[4 * w]);
-                    m2 = fmaxf(m2, red[4 * w + 1]);
-                    m3 = fminf(m3, red[4 * w + 2]);
-                    m4 += reinterpret_cast<int *>(red)[4 * w + 3];
+                    m1 = fmaxf(m1, red[8 * w]);
+                    m2 = fmaxf(m2, red[8 * w + 1]);
+                    m3 = fminf(m3, red[8 * w + 2]);
+                    m4 += reinterpret_cast<int *>(red)[8 * w + 3];
+                    m5 = fmaxf(m5, red[8 * w + 4]);
+                    m6 += reinterpret_cast<unsigned int *>(red)[8 * w + 5];
                 }
                 atomic_max_d(&A.stats->err, (double)m1);
                 atomic_max_d(&A.stats->rmax, (double)m2);
                 atomic_min_d(&A.stats->min_margin, (double)m3);
                 if (m4 > 0) atomicAdd(&A.stats->accepts, (unsigned long long)m4);
+                if (m5 > 0.0f) atomic_max_d(&A.stats->dmax, (double)m5);
+                if (m6) atomicAdd(&A.stats->resets, (unsigned long long)m6);
+            }
+        }
+        if (fused) {
+            // the last tile to finish resets the ticket and advances the epoch for the next launch
+            named_bar(1, kEpiThreads);
+            if (tid == 0) {
+                __threadfence();
+                const unsigned int dn = atomicAdd(&A.fs_ctl->done, 1u);
+                if (dn == gridDim.x - 1) {
+                    A.fs_ctl->ticket = 0;
+                    A.fs_ctl->done = 0;
+                    A.fs_ctl->epoch = A.fs_ctl->epoch + 1u;
+                    __threadfence();
+                }
             }
         }
     }

@@ -415,8 +415,22 @@ struct Plan {
     size_t o_flags = 0, o_agg = 0, o_incl = 0, o_tmp = 0, o_img = 0;
     bool tc = false;
     int tiles = 0, tile_t = 0;
+    // Newton update fused into the tensor-core evaluate kernel: second iterate buffer, and flags
+    // and aggregates of its 128-timestep tiles
+    bool fused = false;
+    int ftiles = 0;
+    size_t o_salt = 0, o_fflags = 0, o_fagg = 0;
     size_t bytes = 0;
 };
+
+// The fused evaluate-and-update path: the tensor-core evaluate kernel in FP32 (the bfloat16
+// pair variant keeps the separate scan, which is what stores the pairs in bfloat16).
+// PMCMC_FUSED_UPDATE=0 selects the separate scan (measurements).
+static bool fused_update(bool tc, const pmcmc_options *o) {
+    if (!tc || o->precision != PMCMC_F32) return false;
+    const char *e = getenv("PMCMC_FUSED_UPDATE");
+    return !(e && e[0] == '0');
+}
 
 static Plan make_plan(const pmcmc_target *tg, const pmcmc_options *o, int T, bool gen_noise,
                       bool need_tmp) {
@@ -456,6 +470,13 @@ static Plan make_plan(const pmcmc_target *tg, const pmcmc_options *o, int T, boo
     p.o_agg = cv.take((size_t)rb * p.tiles * ((size_t)D * D + 2 * D));
     p.o_incl = cv.take((size_t)rb * p.tiles * D);
     if (need_tmp) p.o_tmp = cv.take((size_t)rb * T * D);
+    p.fused = fused_update(p.tc, o);
+    if (p.fused) {
+        p.ftiles = ceil_div(T, kTcTileT);
+        p.o_salt = cv.take((size_t)rb * T * D);
+        p.o_fflags = cv.take(sizeof(unsigned int) * (size_t)p.ftiles);
+        p.o_fagg = cv.take(sizeof(float) * (size_t)p.ftiles * 64);
+    }
     p.bytes = cv.used;
     return p;
 }
@@ -541,6 +562,15 @@ __global__ void loop_ctl_kernel(CtlBlock *c, cudaGraphConditionalHandle h, doubl
     }
 }
 
+// Fused update: the iterate of Newton iteration k lives in s_out for even k and in s_alt for
+// odd k; after the loop the returned iterate is copied to s_out when it is in s_alt.
+__global__ void select_result_kernel(const CtlBlock *c, float *__restrict__ s_out,
+                                     const float *__restrict__ s_alt, size_t n) {
+    if ((c->iter & 1) == 0) return;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        s_out[i] = s_alt[i];
+}
+
 __global__ void loop_init_kernel(CtlBlock *c) {
     c->iter = 0;
     c->skip = 0;
@@ -598,7 +628,7 @@ static pmcmc_status build_loop_graph(pmcmc_ctx *c, const std::string &key, const
                 loop_ctl_kernel<<<1, 1, 0, cs>>>(c->ctl, h, o->atol, max_iters);
                 e = cudaGetLastError();
             }
-            if (e == cudaSuccess) {
+            if (e == cudaSuccess && !p.fused) {  // the fused evaluate kernel applied the update
                 if (o->jac == PMCMC_JAC_DENSE)
                     e = launch_scan_dense(f64, A.T, A.D, p.tile_t, A.a_out, A.b_out, s_out, s0, w,
                                           A.stats, &c->ctl->skip, spin, cs);
@@ -667,6 +697,8 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         c->flags_offset = p.o_flags;
         c->flags_zeroed = p.tiles;
     }
+    // the fused update's flags: this region may have held other data since its last use
+    if (p.fused) PM_CUDA(c, cudaMemsetAsync(base + p.o_fflags, 0, sizeof(unsigned int) * p.ftiles, st));
     // inputs
     if (gen) {
         xi = base + p.o_xi;
@@ -728,23 +760,37 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     if (p.tc) A.tc_img = base + p.o_img;
     A.timeout = &c->ctl->scan.timeout;
     A.spin_limit = spin;
+    if (p.fused) {
+        A.a_out = nullptr;  // the pairs never leave the kernel
+        A.b_out = nullptr;
+        A.s_alt = base + p.o_salt;
+        A.fs_flags = (unsigned int *)(base + p.o_fflags);
+        A.fs_agg = (float *)(base + p.o_fagg);
+        A.fs_ctl = &c->ctl->scan;
+    }
     const double atol = o->atol;
 
     CtlBlock *h = c->host_ctl;
     if (!c->prof_on && !c->no_graph) {
         char kb[768];
         snprintf(kb, sizeof(kb),
-                 "%llu|%d|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%d|%.17g|%d|%d|%.17g|%.17g|%d|%u|%llu|%u|%d|"
+                 "%llu|%d|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%d|%.17g|%d|%d|%.17g|%.17g|%d|%u|%llu|%u|%d|%d|"
                  "%p|%p|%p|%p|%p|%p|%p|%p|%p",
                  c->ws_generation, T, D, tg->N, (int)tg->kind, (int)o->sampler, o->leapfrog_L,
                  (int)o->jac, o->step, tg->prior_scale, (int)o->precision, o->damping, o->clip,
-                 o->gate_grad, o->atol, o->rtol, max_iters, spin, o->seed, o->chain_id, o->engine, s0, s_out,
+                 o->gate_grad, o->atol, o->rtol, max_iters, spin, o->seed, o->chain_id, o->engine, (int)p.fused,
+                 s0, s_out,
                  xi, (const void *)u, tg->mean, tg->prec, tg->X, tg->y, (void *)base);
         pmcmc_status gs = build_loop_graph(c, kb, tg, o, A, p, w, s_out, s0, max_iters, spin);
         if (gs == PMCMC_OK && res_dev) {  // enqueue only: the result lands in device memory
             loop_init_kernel<<<1, 1, 0, st>>>(c->ctl);
             PM_CUDA(c, cudaGetLastError());
             PM_CUDA(c, cudaGraphLaunch(c->graph_exec, st));
+            if (p.fused) {
+                select_result_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(
+                    c->ctl, (float *)s_out, (const float *)(base + p.o_salt), (size_t)T * D);
+                PM_CUDA(c, cudaGetLastError());
+            }
             write_result_kernel<<<1, 1, 0, st>>>(c->ctl, T, res_dev);
             PM_CUDA(c, cudaGetLastError());
             return PMCMC_OK;
@@ -754,6 +800,11 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
             loop_init_kernel<<<1, 1, 0, st>>>(c->ctl);
             PM_CUDA(c, cudaGetLastError());
             PM_CUDA(c, cudaGraphLaunch(c->graph_exec, st));
+            if (p.fused) {
+                select_result_kernel<<<grid_for((size_t)T * D), 256, 0, st>>>(
+                    c->ctl, (float *)s_out, (const float *)(base + p.o_salt), (size_t)T * D);
+                PM_CUDA(c, cudaGetLastError());
+            }
             PM_CUDA(c, cudaEventRecord(c->ev1, st));
             PM_CUDA(c, cudaMemcpyAsync(h, c->ctl, sizeof(CtlBlock), cudaMemcpyDeviceToHost, st));
             PM_CUDA(c, cudaStreamSynchronize(st));
@@ -817,6 +868,11 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
             break;
         }
         if (it >= max_iters) break;
+        if (p.fused) {  // the evaluate kernel wrote the next iterate to the other buffer
+            it++;
+            if (h->scan.timeout) break;
+            continue;
+        }
         prof_begin(c, 2, st);
         if (o->jac == PMCMC_JAC_DENSE)
             PM_CUDA(c, launch_scan_dense(f64, T, D, p.tile_t, A.a_out, A.b_out, s_out, s0, w, stats,
@@ -833,6 +889,8 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
         c->resets_accum += h->stats[0].resets;
         if (h->scan.timeout) break;
     }
+    if (p.fused && (it & 1))
+        PM_CUDA(c, cudaMemcpyAsync(s_out, base + p.o_salt, (size_t)rb * T * D, cudaMemcpyDeviceToDevice, st));
     PM_CUDA(c, cudaEventRecord(c->ev1, st));
     PM_CUDA(c, cudaEventSynchronize(c->ev1));
     float ms = 0.f;

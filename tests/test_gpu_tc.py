@@ -164,3 +164,41 @@ def test_tc_wait_bound_returns_timeout_and_context_recovers():
     upto = ties[0] if len(ties) else T2
     s = npy(s)
     assert np.all(np.abs(s[:upto] - ref[:upto]) <= 1e-5 * (1 + np.abs(ref[:upto])))
+
+
+@pytest.mark.parametrize("T", [1, 127, 128, 129, 5157, 20000])
+def test_fused_update_matches_separate_scan(T):
+    """The Newton update fused into the tensor-core evaluate kernel (look-back over its
+    128-timestep tiles, iterate ping-pong) gives the same solve as the separate scan kernel, on
+    ragged T and on more tiles than SMs (T = 20000: 157 tiles), in the device-side loop and in the
+    host loop (profiling on)."""
+    import os
+    X, y, _ = W.blr_data(300, 9, seed=5)
+    gt = P.Target("logreg", 9, X=cu(X, torch.float32), y=cu(y, torch.float32))
+    xi, u = W.noise(T, 9, seed=6)
+    xid, ud = cu(xi.astype(np.float32), torch.float32), cu(u, torch.float64)
+    s0 = cu(np.zeros(9), torch.float32)
+    opt = P.Options(sampler="mala", step=0.02, jac="diag", precision="f32", atol=1e-6, clip=1,
+                    gate_grad=0)
+    out = {}
+    for mode in ("fused", "separate"):
+        old = os.environ.get("PMCMC_FUSED_UPDATE")
+        os.environ["PMCMC_FUSED_UPDATE"] = "1" if mode == "fused" else "0"
+        try:
+            s, res = P.pmcmc_solve(gt, opt, T, s0, xi=xid, u=ud)
+            P.pmcmc_profile_enable(True)
+            sh, resh = P.pmcmc_solve(gt, opt, T, s0, xi=xid, u=ud)
+            P.pmcmc_profile_enable(False)
+            torch.cuda.synchronize()
+        finally:
+            if old is None:
+                os.environ.pop("PMCMC_FUSED_UPDATE")
+            else:
+                os.environ["PMCMC_FUSED_UPDATE"] = old
+        assert res["status"] == "OK" and resh["status"] == "OK"
+        assert abs(res["iters"] - resh["iters"]) <= 1
+        np.testing.assert_allclose(npy(sh), npy(s), rtol=0, atol=1e-5)
+        out[mode] = (npy(s), res["iters"])
+    assert abs(out["fused"][1] - out["separate"][1]) <= 2
+    err = np.abs(out["fused"][0] - out["separate"][0]) / (1 + np.abs(out["separate"][0]))
+    assert err.max() <= 2e-5, err.max()
