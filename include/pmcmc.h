@@ -91,9 +91,12 @@ typedef enum {
     PMCMC_JAC_ZERO = 4
 } pmcmc_jac;
 
-/* Arithmetic: F64 everywhere; F32 states/f/J with the MH log-ratio accumulated and compared
- * in FP64; F32_SCAN_BF16 as F32 but the scan's affine pairs (J_t, r_t) stored as bfloat16 and
- * combined in FP32 (the Newton loop refines the solve; r_t is always formed in FP32). */
+/* Arithmetic: F64 everywhere; F32 states/f/J with the MH log-ratio's log-likelihood difference
+ * accumulated in compensated FP32 and the ratio and its comparison with log u in FP64;
+ * F32_SCAN_BF16 as F32 but the scan's affine pairs stored as bfloat16 and combined in FP32, and
+ * for DENSE Jacobians (4 < D <= 32) the D x D compositions of the scan run on the tensor cores
+ * with bfloat16 operands and FP32 accumulation (the Newton loop refines the solve; r_t is
+ * always formed in FP32). */
 typedef enum { PMCMC_F64 = 0, PMCMC_F32 = 1, PMCMC_F32_SCAN_BF16 = 2 } pmcmc_precision;
 
 typedef struct {
@@ -234,7 +237,8 @@ pmcmc_status pmcmc_linearize(pmcmc_ctx *ctx, const pmcmc_target *target,
  * The parallel affine scan alone (step (b), Section 2): for t = 0..T-1,
  *   delta_t = a_t (.) delta_{t-1} + b_t  (delta_{-1} = 0),   s_t <- s_t + delta_t.
  * kind PMCMC_JAC_DIAG: a, b are T x D (elementwise maps, quasi-DEER Eq. 4);
- * kind PMCMC_JAC_DENSE: a is T x D x D row-major (a_t delta is a matrix-vector product), b T x D.
+ * kind PMCMC_JAC_DENSE: a is T x D x D row-major (a_t delta is a matrix-vector product), b T x D,
+ *   D <= 32 (F32_SCAN_BF16: 4 < D <= 32, the compositions of a on the tensor cores).
  * precision: F64 (a, b, s double), F32 (float), F32_SCAN_BF16 (a, b bfloat16, s float).
  * s: T x D device, updated in place.  Single pass, decoupled look-back.
  */

@@ -784,22 +784,22 @@ bool logreg_tc_supported(const EvalArgs &A) {
 // the chunk images, then X^T y (kDP floats)
 size_t logreg_tc_image_bytes(int N) { return (size_t)ceil_div(N, kNB) * kImg + kDP * sizeof(float); }
 
-// X^T y (FP64 sums, rounded once), after the chunk images; padded dimensions are zero
+// X^T y (FP64 sums, rounded once), after the chunk images; padded dimensions are zero.  One
+// CTA per dimension.
 __global__ void logreg_tc_xty_kernel(const float *__restrict__ X, const float *__restrict__ y, int N, int D,
                                      float *__restrict__ xty) {
-    __shared__ double part[256];
-    for (int d = 0; d < kDP; d++) {
-        double acc = 0.0;
-        if (d < D)
-            for (int n = threadIdx.x; n < N; n += blockDim.x) acc += (double)y[n] * (double)X[(size_t)n * D + d];
-        part[threadIdx.x] = acc;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) xty[d] = (float)part[0];
-        __syncthreads();
+    __shared__ double part[8];
+    const int d = blockIdx.x;
+    double acc = 0.0;
+    if (d < D)
+        for (int n = threadIdx.x; n < N; n += blockDim.x) acc += (double)y[n] * (double)X[(size_t)n * D + d];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+        xty[d] = (float)t;
     }
 }
 
@@ -808,7 +808,7 @@ cudaError_t launch_logreg_tc_pack(const void *X, const void *y, int N, int D, vo
     logreg_tc_pack_kernel<<<ceil_div(N, kNB), 256, 0, st>>>(static_cast<const float *>(X),
                                                            static_cast<const float *>(y), N, D,
                                                            static_cast<unsigned char *>(img));
-    logreg_tc_xty_kernel<<<1, 256, 0, st>>>(static_cast<const float *>(X), static_cast<const float *>(y), N, D,
+    logreg_tc_xty_kernel<<<kDP, 256, 0, st>>>(static_cast<const float *>(X), static_cast<const float *>(y), N, D,
                                             reinterpret_cast<float *>(static_cast<unsigned char *>(img) +
                                                                       (size_t)ceil_div(N, kNB) * kImg));
     return cudaGetLastError();

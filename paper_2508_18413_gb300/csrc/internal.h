@@ -39,6 +39,13 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st);
 
+// Dense scan with the compositions on the tensor cores (bfloat16 products, FP32 accumulation),
+// 4 < D <= 32: b bfloat16; a bfloat16 (a_bf16) or float.  Tiles of 4 chunks of `chunk` steps.
+int dense_tc_chunk(int T);
+cudaError_t launch_scan_dense_tc(bool a_bf16, int T, int D, int chunk, const void *a, const void *b,
+                                 void *s, const void *s_reset, const ScanWork &w, EvalStats *stats,
+                                 const int *skip, unsigned int spin_limit, cudaStream_t st);
+
 cudaError_t launch_scan_dense(bool f64, int T, int D, int chunk, const void *a, const void *b,
                               void *s, const void *s_reset, const ScanWork &w, EvalStats *stats,
                               const int *skip, unsigned int spin_limit, cudaStream_t st);

@@ -277,10 +277,14 @@ pmcmc_status pmcmc_scan(pmcmc_ctx *c, pmcmc_jac kind, pmcmc_precision prec, int 
         tiles = ceil_div(T, tile_t);
     } else if (kind == PMCMC_JAC_DENSE) {
         if (D > 32) return fail(c, PMCMC_EUNSUPPORTED, "scan: dense scan supports D <= 32");
-        if (prec == PMCMC_F32_SCAN_BF16)
-            return fail(c, PMCMC_EUNSUPPORTED, "scan: dense scan has no bfloat16 storage");
-        tile_t = dense_scan_chunk(T, D);
-        tiles = ceil_div(T, tile_t);
+        if (prec == PMCMC_F32_SCAN_BF16) {  // compositions on the tensor cores
+            if (D <= 4) return fail(c, PMCMC_EUNSUPPORTED, "scan: bfloat16 dense scan needs D > 4");
+            tile_t = dense_tc_chunk(T);
+            tiles = ceil_div(T, 4 * tile_t);
+        } else {
+            tile_t = dense_scan_chunk(T, D);
+            tiles = ceil_div(T, tile_t);
+        }
     } else {
         return fail(c, PMCMC_EINVAL, "scan: kind must be DIAG or DENSE");
     }
@@ -306,6 +310,9 @@ pmcmc_status pmcmc_scan(pmcmc_ctx *c, pmcmc_jac kind, pmcmc_precision prec, int 
     if (kind == PMCMC_JAC_DIAG)
         PM_CUDA(c, launch_scan_diag(f64, prec == PMCMC_F32_SCAN_BF16 ? 1 : 0, T, D, tile_t, a, b,
                                     s, nullptr, w, nullptr, nullptr, kDefaultSpinLimit, st));
+    else if (prec == PMCMC_F32_SCAN_BF16)
+        PM_CUDA(c, launch_scan_dense_tc(true, T, D, tile_t, a, b, s, nullptr, w, nullptr, nullptr,
+                                        kDefaultSpinLimit, st));
     else
         PM_CUDA(c, launch_scan_dense(f64, T, D, tile_t, a, b, s, nullptr, w, nullptr, nullptr,
                                      kDefaultSpinLimit, st));
@@ -367,8 +374,8 @@ pmcmc_status check_problem(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opt
         return fail(c, PMCMC_EINVAL, "BLOCK2 Jacobian is for PMCMC_HMC_PAR_LEAPFROG");
     if (o->jac == PMCMC_JAC_DENSE) {
         if (D > 32) return fail(c, PMCMC_EUNSUPPORTED, "dense Newton supports D <= 32");
-        if (o->precision == PMCMC_F32_SCAN_BF16)
-            return fail(c, PMCMC_EUNSUPPORTED, "dense Newton has no bfloat16 scan");
+        if (o->precision == PMCMC_F32_SCAN_BF16 && D <= 4)
+            return fail(c, PMCMC_EUNSUPPORTED, "dense Newton with bfloat16 compositions needs D > 4");
         if (tg->kind == PMCMC_LOGREG && o->sampler != PMCMC_MALA)
             return fail(c, PMCMC_EUNSUPPORTED, "dense logreg Jacobian is for MALA");
     }
@@ -441,7 +448,7 @@ static Plan make_plan(const pmcmc_target *tg, const pmcmc_options *o, int T, boo
     const int rb = f64 ? 8 : 4;
     const int sb = o->precision == PMCMC_F32_SCAN_BF16 ? 2 : rb;
     const bool dense = o->jac == PMCMC_JAC_DENSE;
-    p.o_a = cv.take(dense ? (size_t)rb * T * D * D : (size_t)sb * T * D);
+    p.o_a = cv.take(dense ? (size_t)rb * T * D * D : (size_t)sb * T * D);  // dense J in the arithmetic type
     p.o_b = cv.take((size_t)sb * T * D);
     if (gen_noise) {
         p.o_xi = cv.take((size_t)rb * T * D);
@@ -460,12 +467,13 @@ static Plan make_plan(const pmcmc_target *tg, const pmcmc_options *o, int T, boo
         }
     }
     p.o_acc = cv.take((size_t)T);
-    if (dense) {
-        p.tile_t = dense_scan_chunk(T, D);
+    if (dense && o->precision == PMCMC_F32_SCAN_BF16) {  // tensor-core compositions, 4 chunks a tile
+        p.tile_t = dense_tc_chunk(T);
+        p.tiles = std::max(1, ceil_div(T, 4 * p.tile_t));
     } else {
-        p.tile_t = diag_scan_tile(T, D, rb);
+        p.tile_t = dense ? dense_scan_chunk(T, D) : diag_scan_tile(T, D, rb);
+        p.tiles = std::max(1, ceil_div(T, p.tile_t));
     }
-    p.tiles = std::max(1, ceil_div(T, p.tile_t));
     p.o_flags = cv.take(sizeof(unsigned int) * p.tiles);
     p.o_agg = cv.take((size_t)rb * p.tiles * ((size_t)D * D + 2 * D));
     p.o_incl = cv.take((size_t)rb * p.tiles * D);
@@ -629,7 +637,10 @@ static pmcmc_status build_loop_graph(pmcmc_ctx *c, const std::string &key, const
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess && !p.fused) {  // the fused evaluate kernel applied the update
-                if (o->jac == PMCMC_JAC_DENSE)
+                if (o->jac == PMCMC_JAC_DENSE && A.bf16)
+                    e = launch_scan_dense_tc(false, A.T, A.D, p.tile_t, A.a_out, A.b_out, s_out, s0, w,
+                                             A.stats, &c->ctl->skip, spin, cs);
+                else if (o->jac == PMCMC_JAC_DENSE)
                     e = launch_scan_dense(f64, A.T, A.D, p.tile_t, A.a_out, A.b_out, s_out, s0, w,
                                           A.stats, &c->ctl->skip, spin, cs);
                 else
@@ -874,7 +885,10 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
             continue;
         }
         prof_begin(c, 2, st);
-        if (o->jac == PMCMC_JAC_DENSE)
+        if (o->jac == PMCMC_JAC_DENSE && A.bf16)
+            PM_CUDA(c, launch_scan_dense_tc(false, T, D, p.tile_t, A.a_out, A.b_out, s_out, s0, w, stats,
+                                            nullptr, spin, st));
+        else if (o->jac == PMCMC_JAC_DENSE)
             PM_CUDA(c, launch_scan_dense(f64, T, D, p.tile_t, A.a_out, A.b_out, s_out, s0, w, stats,
                                          nullptr, spin, st));
         else
@@ -954,6 +968,8 @@ pmcmc_status window_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     const int rb = f64 ? 8 : 4;
     const int W = o->window;
     const bool gen = xi == nullptr;
+    if (o->jac == PMCMC_JAC_DENSE && bf16)
+        return fail(c, PMCMC_EUNSUPPORTED, "window: dense Newton in FP32 or FP64 (no bfloat16 compositions)");
     Plan p = make_plan(tg, o, W, false, false);
     Carve cv;
     cv.used = p.bytes;
