@@ -122,4 +122,82 @@ __device__ void lookback_block64(const unsigned int *flags, const R *gagg, const
     }
 }
 
+// Shared-memory values per aggregate staged by lookback_dense: D rows of D + 1 (padded) and b.
+__host__ __device__ constexpr int dense_stage_stride(int D) { return D * (D + 1) + D; }
+
+// Dense look-back (D <= 32; tile aggregates are affine maps (A, b), A row-major, D * D + D
+// values per tile in gagg; inclusive values D per tile in gincl).  Warp 0 finds the nearest
+// predecessor with a published inclusive value, 32 flags per round (a ballot picks the nearest
+// lane that saw an inclusive flag or ran past tile 0).  The aggregates of the tiles in between
+// are then staged into shared memory `stage` (nb of them at a time, dense_stage_stride(D)
+// values each; all threads load, each a whole row, rows padded to D + 1 so that lane r reading
+// row r is free of bank conflicts) and warp 0 applies them in order as matrix-vector products,
+// the vector held one component per lane.  A timed-out wait (recorded in ctl) leaves a zero
+// carry.  The carry of component d ends in carry_out[d].  Called by all threads of the block
+// (NT of them, Bar their barrier).
+template <typename R, int NT, class Bar = CtaBar>
+__device__ void lookback_dense(const unsigned int *flags, const R *gagg, const R *gincl, int tile,
+                               int D, unsigned int epoch, unsigned int spin_limit, ScanCtl *ctl,
+                               R *stage, int nb, R *carry_out) {
+    __shared__ int s_jj;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int DD = D * D, SQ = dense_stage_stride(D);
+    const size_t AGG = (size_t)DD + D;
+    if (tid < 32) {
+        int jend = tile - 1, jj = -1;
+        bool timed_out = false;
+        for (;;) {
+            const int j = jend - lane;
+            unsigned int st = kFlagIncl;  // j < 0: the walk ran past tile 0
+            if (j >= 0) st = wait_flag(flags, j, epoch, spin_limit, ctl);
+            const unsigned int stop = __ballot_sync(0xffffffffu, j < 0 || st != kFlagAgg);
+            if (stop) {
+                const int l = __ffs(stop) - 1;
+                const unsigned int stl = __shfl_sync(0xffffffffu, st, l);
+                jj = jend - l;
+                timed_out = jj >= 0 && stl != kFlagIncl;
+                break;
+            }
+            jend -= 32;
+        }
+        if (lane == 0) s_jj = timed_out ? -2 : jj;
+    }
+    Bar::sync();
+    const int jj = s_jj;
+    R v = R(0);  // warp 0: component `lane` of the running vector
+    if (tid < 32 && jj >= 0 && lane < D) v = __ldcg(gincl + (size_t)jj * D + lane);
+    for (int m0 = (jj == -2 ? tile : jj + 1); m0 < tile; m0 += nb) {
+        const int cnt = min(nb, tile - m0);
+        // stage rows: (aggregate q, row r), r == D is b
+        for (int idx = tid; idx < cnt * (D + 1); idx += NT) {
+            const int q = idx / (D + 1), r = idx - q * (D + 1);
+            const R *src = gagg + (size_t)(m0 + q) * AGG + (size_t)r * D;
+            R *dst = stage + (size_t)q * SQ + r * (D + 1);
+            R tmp[32];
+#pragma unroll
+            for (int c = 0; c < 32; c++) tmp[c] = c < D ? __ldcg(src + c) : R(0);
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+                if (c < D) dst[c] = tmp[c];
+        }
+        Bar::sync();
+        if (tid < 32) {
+            for (int q = 0; q < cnt; q++) {
+                const R *Aq = stage + (size_t)q * SQ;
+                R acc0 = lane < D ? Aq[D * (D + 1) + lane] : R(0), acc1 = R(0);
+#pragma unroll
+                for (int k = 0; k < 32; k += 2) {
+                    const R v0 = __shfl_sync(0xffffffffu, v, k), v1 = __shfl_sync(0xffffffffu, v, k + 1);
+                    if (k < D && lane < D) acc0 = fma(Aq[lane * (D + 1) + k], v0, acc0);
+                    if (k + 1 < D && lane < D) acc1 = fma(Aq[lane * (D + 1) + k + 1], v1, acc1);
+                }
+                v = lane < D ? acc0 + acc1 : R(0);
+            }
+        }
+        Bar::sync();
+    }
+    if (tid < D) carry_out[tid] = v;
+    Bar::sync();
+}
+
 }  // namespace pm

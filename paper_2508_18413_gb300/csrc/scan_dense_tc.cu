@@ -280,44 +280,14 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
     __syncthreads();
     if (tid == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
     float *carry = vec + 32;  // vec[32..63]: the carry into the tile
-    float *wv = vec + 64;     // two work vectors
     if (tid < kP) carry[tid] = 0.0f;
     __syncthreads();
     if (tile > 0) {
-        __shared__ int s_jj;
-        if (tid == 0) {
-            int jj = tile - 1;
-            for (; jj >= 0; jj--) {
-                const unsigned int st = wait_flag(flags, jj, epoch, limit, ctl);
-                if (st == kFlagIncl || st == 0) break;
-            }
-            if (jj >= 0) {
-                const unsigned int st = ld_acquire(flags + jj);
-                if (!((st & 3u) == kFlagIncl && (st >> 2) == (epoch & 0x3fffffffu))) jj = -1;
-            }
-            s_jj = jj;
-        }
-        __syncthreads();
-        const int jj = s_jj;
-        int vc = 0;
-        if (tid < kP) wv[tid] = (jj >= 0 && tid < D) ? __ldcg(gincl + (size_t)jj * D + tid) : 0.0f;
-        __syncthreads();
-        for (int m = max(jj + 1, 0); m < tile; m++) {
-            const float *Am = gagg + (size_t)m * AGG;
-            float acc = 0.0f;
-            if (tid < D) {
-                acc = __ldcg(Am + DD + tid);
-#pragma unroll
-                for (int k = 0; k < kP; k++)
-                    if (k < D) acc = fmaf(__ldcg(Am + tid * D + k), wv[vc * 32 + k], acc);
-            }
-            __syncthreads();
-            if (tid < kP) wv[(vc ^ 1) * 32 + tid] = tid < D ? acc : 0.0f;
-            __syncthreads();
-            vc ^= 1;
-        }
-        if (tid < kP) carry[tid] = wv[vc * 32 + tid];
-        __syncthreads();
+        // the A and B operand buffers are free after phase A: they stage the aggregates
+        constexpr int kStageBytes = 2 * kABuf + 2 * kBRegion;
+        const int nb = min(32, kStageBytes / (int)(sizeof(float) * dense_stage_stride(D)));
+        lookback_dense<float, kThreads>(flags, gagg, gincl, tile, D, epoch, limit, ctl,
+                                        reinterpret_cast<float *>(sm + oA), nb, carry);
         if (tid < D) {  // inclusive value of this tile = TA carry + tb
             float acc = vec[tid];
             for (int k = 0; k < D; k++) acc = fmaf(TA[tid * kPStride + k], carry[k], acc);
