@@ -16,6 +16,7 @@ data path; the reported time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -94,9 +95,11 @@ def parse():
     ap.add_argument("--workload", default="c2",
                     choices=["c2", "c1", "c3_diag", "c3_bf16", "c3_block", "c4", "c5",
                              "gibbs_diag", "gibbs_dense", "adjoint_small", "c3_paper",
-                             "scan_sweep", "dense_scan"],
+                             "scan_sweep", "dense_scan", "dense_newton"],
                     help="c2 (default) is the headline line; the others measure the other "
                          "configurations")
+    ap.add_argument("--dense-max-iters", type=int, default=0,
+                    help="dense_newton workload: Newton iterations per solve (0: to convergence)")
     ap.add_argument("--basis", action="store_true",
                     help="solve in the eigenbasis of X^T X (Section 3.4 reparameterisation)")
     ap.add_argument("--gate-grad", type=int, default=0,
@@ -650,11 +653,13 @@ def run_ours(args):
         seq_ms = e0.elapsed_time(e1)
 
     # --- dense-Newton line (same chain), run to convergence (it needs thousands of iterations:
-    # the dense linearisation of this chain is expanding), timed once -----------------------
+    # the dense linearisation of this chain is expanding), timed once.  Held gate, damping 0.5
+    # (6,271 iterations against 9,326 undamped and 11,640 with the gate term), the Jacobian
+    # assembled and the scan's compositions done on the tensor cores ---------------------------
     dense = None
     if rank == 0 and not args.no_variants:
-        optd = P.Options(sampler="mala", step=WL.step, jac="dense", precision="f32", atol=WL.tol,
-                         clip=CLIP, max_iters=WL.T)
+        optd = P.Options(sampler="mala", step=WL.step, jac="dense", precision="f32_scan_bf16", atol=WL.tol,
+                         clip=CLIP, max_iters=WL.T, gate_grad=0, damping=0.5)
         torch.cuda.synchronize()
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -664,7 +669,8 @@ def run_ours(args):
         e1.synchronize()
         dms = e0.elapsed_time(e1)
         dense = {"value": WL.T / (dms / 1000.0), "unit": UNIT, "ms": dms, "newton_iters": rd["iters"],
-                 "status": rd["status"]}
+                 "status": rd["status"], "how": "dense J (tcgen05 tf32), held gate, damping 0.5, clip, "
+                 "scan compositions on tcgen05 (bfloat16), residual atol " + str(WL.tol)}
 
     configs, keep = None, None
     if rank == 0 and not args.no_variants:
@@ -986,6 +992,41 @@ def run_other(args):
                     converged=sum(r["status"] == "OK" for r in res), dtype="f32",
                     seq_gpu={"value": total / (sms / 1e3), "ms": sms, "speedup": sms / ms,
                              "how": "one sequential kernel per chain on 16 streams"})
+    elif wl == "dense_newton":
+        # the headline chain solved by dense Newton (DEER, Eq. 3): the logistic J assembled on
+        # the tensor cores, the scan's compositions on the tensor cores; per-kernel device time
+        # from the library's profile counters.  --dense-max-iters bounds the solve (a bounded run
+        # measures the cost per iteration; the default runs to convergence)
+        X, y, _ = W.blr_data(W.C2.N, W.C2.D, seed=W.C2.seed, dtype=np.float32)
+        xi_h, u_h = W.noise(W.C2.T, W.C2.D, seed=0, dtype=np.float32)
+        tgt = P.Target("logreg", W.C2.D, X=torch.tensor(X, device=dev), y=torch.tensor(y, device=dev),
+                       prior_scale=1.0)
+        xid, ud = torch.tensor(xi_h, device=dev), torch.tensor(u_h, device=dev)
+        s0 = torch.zeros(W.C2.D, dtype=torch.float32, device=dev)
+        rows = []
+        for engine in ("auto", "simt"):
+            optd = P.Options(sampler="mala", step=W.C2.step, jac="dense", precision="f32_scan_bf16",
+                             atol=W.C2.tol, clip=1, gate_grad=0, damping=0.5, engine=engine,
+                             max_iters=args.dense_max_iters or W.C2.T)
+            P.pmcmc_solve(tgt, dataclasses.replace(optd, max_iters=3), W.C2.T, s0, xi=xid, u=ud)  # warm-up
+            torch.cuda.synchronize()
+            P.pmcmc_profile_enable(True)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, rd = P.pmcmc_solve(tgt, optd, W.C2.T, s0, xi=xid, u=ud)
+            e1.record(stream)
+            e1.synchronize()
+            pr = P.pmcmc_profile_get()
+            P.pmcmc_profile_enable(False)
+            ms = e0.elapsed_time(e1)
+            it = max(rd["iters"], 1)
+            rows.append({"engine": engine, "ms": ms, "newton_iters": rd["iters"], "status": rd["status"],
+                         "value": W.C2.T / (ms / 1e3), "ms_per_iter": ms / it,
+                         "eval_ms_per_iter": pr["eval_ms"] / it, "jac_ms_per_iter": pr["jac_ms"] / it,
+                         "scan_ms_per_iter": pr["scan_ms"] / it})
+        line.update(config="C2 chain (MALA logistic N=1000, D=25, T=16384, step 0.01) by dense Newton: "
+                           "held gate, damping 0.5, clip, bfloat16 scan pairs", unit=UNIT, rows=rows)
     elif wl == "dense_scan":
         # the dense scan alone (DEER's linear solve, Eq. 3): compositions on the CUDA cores
         # (FP32) against the tensor cores (bfloat16 operands, FP32 accumulation)

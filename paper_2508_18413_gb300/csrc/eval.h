@@ -54,6 +54,9 @@ struct EvalArgs {
     const void *tc_img = nullptr;     // chunk images of the design (launch_logreg_tc_pack)
     unsigned int *timeout = nullptr;  // set to 1 when a bounded wait ran out
     unsigned int spin_limit = 0;      // polls per wait; 0 = default
+    // tensor-core dense Jacobian (logistic MALA, D <= 32): pair image of the design
+    // (launch_logreg_pair_pack); null selects the CUDA-core assembly
+    const void *pair_img = nullptr;
     // Newton update fused into the tensor-core evaluate kernel (fs_flags non-null): the kernel
     // also solves delta_t = J_t delta_{t-1} + r_t (carry from the published aggregates of the
     // earlier tiles) and writes s + delta to the other iterate buffer.  The parity of *iter
@@ -81,5 +84,11 @@ size_t logreg_tc_image_bytes(int N);
 cudaError_t launch_logreg_tc_pack(const void *X, const void *y, int N, int D, void *img, cudaStream_t st);
 cudaError_t launch_eval_logreg_tc(const EvalArgs &A, cudaStream_t st);
 constexpr int kTcTileT = 128;  // timesteps per CTA of the tensor-core evaluate kernel
+
+// tensor-core assembly of the dense logistic-MALA Jacobian (jac_logreg_tc.cu)
+bool logreg_jac_tc_supported(const EvalArgs &A);
+size_t logreg_pair_image_bytes(int N, int D);
+cudaError_t launch_logreg_pair_pack(const void *X, int N, int D, void *img, cudaStream_t st);
+cudaError_t launch_jac_logreg_tc(const EvalArgs &A, cudaStream_t st);
 
 }  // namespace pm

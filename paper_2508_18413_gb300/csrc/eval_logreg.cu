@@ -470,6 +470,7 @@ cudaError_t launch_eval_logreg(const EvalArgs &A, cudaStream_t st) {
 }
 
 cudaError_t launch_logreg_dense_jac(const EvalArgs &A, cudaStream_t st) {
+    if (A.pair_img && !A.f64) return launch_jac_logreg_tc(A, st);
     const int DP = logreg_padded_dim(A.D);
     const int blocks = ceil_div(A.T, 8);
 #define PM_DJ(R_)                                                                             \

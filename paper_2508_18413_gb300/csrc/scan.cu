@@ -1182,9 +1182,6 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
     return run_scan_diag<float, float>(T, D, tile_t, a, b, s, s_reset, w, stats, skip, spin_limit, st);
 }
 
-// shared memory that stages the tile aggregates of the dense look-back (dynamic)
-constexpr int kDenseStageBytes = 24 * 1024;
-
 // ==========================================================================================
 // Dense scan (DEER, Eq. 3), D <= 32: one CTA per chunk of C timesteps.
 //   Phase A: chunk aggregate (Phi, beta) = composition of its (J_t, b_t), sequential matmuls.
@@ -1247,18 +1244,41 @@ scan_dense_kernel(int T, int D, int C, const R *__restrict__ a, const R *__restr
     }
     __syncthreads();
     if (tid == 0) st_release(flags + tile, make_flag(epoch, tile == 0 ? kFlagIncl : kFlagAgg));
+    __shared__ int s_jj;
     if (tile > 0) {
-        extern __shared__ __align__(16) unsigned char dense_stage_raw[];
-        R *stage = reinterpret_cast<R *>(dense_stage_raw);
-        const int nb = min(32, kDenseStageBytes / (int)(sizeof(R) * dense_stage_stride(D)));
-        lookback_dense<R, kScanThreads>(flags, gagg, gincl, tile, D, epoch, spin_limit, ctl, stage, nb,
-                                        vec[1]);
+        if (tid == 0) {
+            int jj = tile - 1;
+            for (; jj >= 0; jj--) {
+                unsigned int st = wait_flag(flags, jj, epoch, spin_limit, ctl);
+                if (st == kFlagIncl || st == 0) break;
+            }
+            if (jj >= 0) {
+                unsigned int st = ld_acquire(flags + jj);
+                if (!((st & 3u) == kFlagIncl && (st >> 2) == (epoch & 0x3fffffffu))) jj = -1;
+            }
+            s_jj = jj;
+        }
+        __syncthreads();
+        const int jj = s_jj;
+        int vc = 0;
+        if (tid < D) vec[0][tid] = jj >= 0 ? gincl[(size_t)jj * D + tid] : R(0);
+        __syncthreads();
+        for (int m = max(jj + 1, 0); m < tile; m++) {
+            const R *Am = gagg + (size_t)m * AGG;
+            if (tid < D) {
+                R acc = Am[DD + tid];
+                for (int k = 0; k < D; k++) acc += Am[tid * D + k] * vec[vc][k];
+                vec[vc ^ 1][tid] = acc;
+            }
+            __syncthreads();
+            vc ^= 1;
+        }
         // inclusive = Phi * carry + beta
         if (tid < D) {
             R acc = beta[cur][tid];
-            for (int k = 0; k < D; k++) acc += Phi[cur][tid * D + k] * vec[1][k];
+            for (int k = 0; k < D; k++) acc += Phi[cur][tid * D + k] * vec[vc][k];
             gincl[(size_t)tile * D + tid] = acc;
-            vec[0][tid] = vec[1][tid];  // carry
+            vec[0][tid] = vec[vc][tid];  // carry
         }
         __threadfence();
         __syncthreads();
@@ -1471,9 +1491,7 @@ template <typename R, int DM>
 static cudaError_t run_scan_dense(int T, int D, int C, const void *a, const void *b, void *s,
                                   const void *s_reset, const ScanWork &w, EvalStats *stats,
                                   const int *skip, unsigned int spin, cudaStream_t st) {
-    cudaError_t e = ensure_dyn_smem(scan_dense_kernel<R, DM>, kDenseStageBytes);
-    if (e != cudaSuccess) return e;
-    scan_dense_kernel<R, DM><<<ceil_div(T, C), kScanThreads, kDenseStageBytes, st>>>(
+    scan_dense_kernel<R, DM><<<ceil_div(T, C), kScanThreads, 0, st>>>(
         T, D, C, (const R *)a, (const R *)b, (R *)s, (const R *)s_reset, w.flags, (R *)w.agg,
         (R *)w.incl, w.ctl, stats, skip, spin);
     return cudaGetLastError();

@@ -416,11 +416,18 @@ static bool uses_tc(const pmcmc_target *tg, const pmcmc_options *o, int T) {
     return logreg_tc_supported(A);
 }
 
+// Whether the dense Jacobian of this problem is assembled on the tensor cores.
+static bool uses_jac_tc(const pmcmc_target *tg, const pmcmc_options *o, int T) {
+    EvalArgs A;
+    fill_eval_args(A, tg, o, T);
+    return logreg_jac_tc_supported(A);
+}
+
 // Workspace plan for one solve.
 struct Plan {
     size_t o_a = 0, o_b = 0, o_xi = 0, o_u = 0, o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0;
-    size_t o_flags = 0, o_agg = 0, o_incl = 0, o_tmp = 0, o_img = 0;
-    bool tc = false;
+    size_t o_flags = 0, o_agg = 0, o_incl = 0, o_tmp = 0, o_img = 0, o_pimg = 0;
+    bool tc = false, jtc = false;
     int tiles = 0, tile_t = 0;
     // Newton update fused into the tensor-core evaluate kernel: second iterate buffer, and flags
     // and aggregates of its 128-timestep tiles
@@ -464,6 +471,8 @@ static Plan make_plan(const pmcmc_target *tg, const pmcmc_options *o, int T, boo
             p.o_w = cv.take((size_t)rb * T * tg->N);
             p.o_ru = cv.take((size_t)rb * T * D);
             p.o_rv = cv.take((size_t)rb * T * D);
+            p.jtc = uses_jac_tc(tg, o, T);
+            if (p.jtc) p.o_pimg = cv.take(logreg_pair_image_bytes(tg->N, D));
         }
     }
     p.o_acc = cv.take((size_t)T);
@@ -728,6 +737,10 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
             PM_CUDA(c, launch_logreg_tc_pack(tg->X, tg->y, tg->N, D, base + p.o_img, st));
             prof_count(c);
         }
+        if (p.jtc) {
+            PM_CUDA(c, launch_logreg_pair_pack(tg->X, tg->N, D, base + p.o_pimg, st));
+            prof_count(c);
+        }
     }
     // initial guess: s^(0) = s_init, or s0 broadcast (Appendix B)
     if (s_init) {
@@ -769,6 +782,7 @@ pmcmc_status newton_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     const int max_iters = o->max_iters > 0 ? o->max_iters : T;
     const unsigned int spin = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
     if (p.tc) A.tc_img = base + p.o_img;
+    if (p.jtc) A.pair_img = base + p.o_pimg;
     A.timeout = &c->ctl->scan.timeout;
     A.spin_limit = spin;
     if (p.fused) {
@@ -998,6 +1012,7 @@ pmcmc_status window_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
                                                                      D, Npad, DP, rb);
         PM_CUDA(c, cudaGetLastError());
         if (p.tc) PM_CUDA(c, launch_logreg_tc_pack(tg->X, tg->y, tg->N, D, base + p.o_img, st));
+        if (p.jtc) PM_CUDA(c, launch_logreg_pair_pack(tg->X, tg->N, D, base + p.o_pimg, st));
     }
     if (s_init) {
         if (s_init != s_out)
@@ -1029,6 +1044,7 @@ pmcmc_status window_solve(pmcmc_ctx *c, const pmcmc_target *tg, const pmcmc_opti
     A.iter = &c->ctl->iter;
     const unsigned int spin = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
     if (p.tc) A.tc_img = base + p.o_img;
+    if (p.jtc) A.pair_img = base + p.o_pimg;
     A.timeout = &c->ctl->scan.timeout;
     A.spin_limit = spin;
     const int max_iters = o->max_iters > 0 ? o->max_iters : T;
@@ -1146,9 +1162,10 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
     const bool f64 = o->precision == PMCMC_F64;
     const int rb = f64 ? 8 : 4;
     Carve cv;
-    size_t o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0, o_j = 0, o_img = 0;
+    size_t o_xp = 0, o_w = 0, o_ru = 0, o_rv = 0, o_acc = 0, o_j = 0, o_img = 0, o_pimg = 0;
     const bool dense = o->jac == PMCMC_JAC_DENSE;
     const bool tc = uses_tc(tg, o, T);
+    const bool jtc = tg->kind == PMCMC_LOGREG && dense && uses_jac_tc(tg, o, T);
     if (tg->kind == PMCMC_LOGREG) {
         const int DP = logreg_padded_dim(D);
         o_xp = cv.take((size_t)rb * ceil_div(tg->N, 64) * 64 * DP);
@@ -1158,6 +1175,7 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
             o_ru = cv.take((size_t)rb * T * D);
             o_rv = cv.take((size_t)rb * T * D);
             o_acc = cv.take((size_t)T);
+            if (jtc) o_pimg = cv.take(logreg_pair_image_bytes(tg->N, D));
         }
     }
     if (dense && !jac_out) o_j = cv.take((size_t)rb * T * D * D);
@@ -1192,6 +1210,12 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
             A.rank1_u = base + o_ru;
             A.rank1_v = base + o_rv;
             if (!acc_out) A.acc_out = (unsigned char *)(base + o_acc);
+            if (jtc) {
+                PM_CUDA(c, launch_logreg_pair_pack(tg->X, tg->N, D, base + o_pimg, st));
+                A.pair_img = base + o_pimg;
+                A.timeout = &c->ctl->scan.timeout;
+                A.spin_limit = o->spin_limit > 0 ? (unsigned int)o->spin_limit : kDefaultSpinLimit;
+            }
         }
         PM_CUDA(c, launch_eval_logreg(A, st));
         if (dense) PM_CUDA(c, launch_logreg_dense_jac(A, st));
@@ -1199,7 +1223,7 @@ extern "C" pmcmc_status pmcmc_linearize(pmcmc_ctx *c, const pmcmc_target *tg,
         PM_CUDA(c, launch_eval_small(A, st));
     }
     PM_CUDA(c, cudaStreamSynchronize(st));
-    if (tc) {
+    if (tc || jtc) {
         unsigned int to = 0;
         PM_CUDA(c, cudaMemcpy(&to, &c->ctl->scan.timeout, sizeof(to), cudaMemcpyDeviceToHost));
         if (to) {
