@@ -1009,14 +1009,13 @@ void scan_shape_override(int rows, int nsub) {
 }
 
 static void diag_shape(int T, int D, int *rows, int *nsub) {
-    static bool env_read = false;
-    if (!env_read) {  // PMCMC_SCAN_SHAPE="rows,nsub" fixes the shape (measurements)
-        env_read = true;
+    {  // PMCMC_SCAN_SHAPE="rows,nsub" fixes the shape (measurements, tests); read at every call
         const char *e = getenv("PMCMC_SCAN_SHAPE");
         int r = 0, n = 0;
         if (e && sscanf(e, "%d,%d", &r, &n) == 2 && (r == 8 || r == 16) && n >= 1 && n <= 64) {
-            g_shape_rows = r;
-            g_shape_nsub = n;
+            *rows = r;
+            *nsub = n;
+            return;
         }
     }
     *rows = g_shape_rows > 0 ? g_shape_rows : 8;

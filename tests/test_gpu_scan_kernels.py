@@ -106,3 +106,30 @@ def test_scan_kernel_repeated_launches(kernel):
         P.pmcmc_scan("diag", "f32", ag, bg, s)
         np.testing.assert_allclose(s.double().cpu().numpy() - s0.astype(np.float64), delta,
                                    rtol=2e-5, atol=2e-4)
+
+
+@pytest.mark.parametrize("shape", ["8,2", "8,3", "8,6", "8,32", "16,5", "16,16"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f32_scan_bf16"])
+@pytest.mark.parametrize("T,D", [(100003, 8), (40001, 3), (65536, 32)])
+def test_row_kernel_shapes_match_linear_recursion(shape, precision, T, D):
+    """The row kernel with several sub-chunks per warp (PMCMC_SCAN_SHAPE = "rows,sub-chunks"
+    fixes the shape), including counts that are not powers of two and tiles of every size from
+    a few per CTA to a single ragged one."""
+    saved = {k: os.environ.get(k) for k in ("PMCMC_SCAN_KERNEL", "PMCMC_SCAN_SHAPE")}
+    os.environ["PMCMC_SCAN_KERNEL"] = "rows"
+    os.environ["PMCMC_SCAN_SHAPE"] = shape
+    try:
+        rng = np.random.default_rng(T + D + len(shape))
+        a = rng.uniform(-0.98, 0.98, (T, D))
+        b = rng.standard_normal((T, D))
+        s = rng.standard_normal((T, D))
+        a_used, b_used, s_in, out = _run(precision, a, b, s)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    delta = O.linear_recursion(a_used, b_used, dense=False)
+    tol = 1e-12 if precision == "f64" else 2e-5
+    np.testing.assert_allclose(out - s_in, delta, rtol=tol, atol=tol * 10)
