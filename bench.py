@@ -604,9 +604,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof = P.pmcmc_profile_get()
     P.pmcmc_profile_enable(False)
-    # launches inside the timed region: one evaluate per iteration plus one per solve, one
-    # scan per iteration, one control kernel per evaluate, and the solve's set-up kernels
-    launches_timed = sum(3 * r["iters"] + 2 + 5 for r in results)
+    # launches inside the timed region, per solve: iters + 1 evaluations; on the fused path
+    # (the default) each is one kernel that also applies the update and takes the loop's
+    # decision, otherwise evaluate + control + scan; and the set-up kernels (padded design,
+    # tensor-core images and X^T y, initial guess, two finiteness checks, loop init, and the
+    # copy of the result out of the second iterate buffer on the fused path)
+    fused = os.environ.get("PMCMC_FUSED_UPDATE", "1") != "0"
+    launches_timed = sum((r["iters"] + 1) * (1 if fused else 3) + (8 if fused else 7) for r in results)
 
     ms_local = sum(step_ms) / len(step_ms)
 

@@ -9,6 +9,7 @@ namespace pm {
 
 struct EvalStats;
 struct ScanCtl;
+struct CtlBlock;
 
 struct EvalArgs {
     // problem
@@ -65,6 +66,13 @@ struct EvalArgs {
     unsigned int *fs_flags = nullptr;  // one per 128-timestep tile, epoch-tagged
     float *fs_agg = nullptr;           // tiles x 2 x 32: tile aggregates (A, B)
     ScanCtl *fs_ctl = nullptr;         // ticket, done, epoch, timeout
+    // device-side Newton loop (fused path, inside the loop's graph): the last tile to finish
+    // also takes the loop's convergence decision and sets the WHILE condition (null: a separate
+    // control kernel does)
+    CtlBlock *loop = nullptr;
+    unsigned long long loop_handle = 0;  // cudaGraphConditionalHandle
+    double loop_atol = 0.0;
+    int loop_max_iters = 0;
 };
 
 cudaError_t launch_eval_small(const EvalArgs &A, cudaStream_t st);

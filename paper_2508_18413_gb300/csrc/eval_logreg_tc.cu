@@ -38,6 +38,7 @@
 #include "eval.h"
 #include "internal.h"
 #include "lookback.cuh"
+#include "solve.h"
 #include "tc.cuh"
 
 namespace pm {
@@ -729,6 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             // the last tile to finish resets the ticket and advances the epoch for the next launch
             named_bar(1, kEpiThreads);
             if (tid == 0) {
+                if (*abort_f && A.timeout) atomicExch(A.timeout, 1u);  // before counting out
                 __threadfence();
                 const unsigned int dn = atomicAdd(&A.fs_ctl->done, 1u);
                 if (dn == gridDim.x - 1) {
@@ -736,6 +738,11 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     A.fs_ctl->done = 0;
                     A.fs_ctl->epoch = A.fs_ctl->epoch + 1u;
                     __threadfence();
+                    // every tile's statistics (and timeout) were published before it counted
+                    // out: the loop's decision for this iteration can be taken here
+                    if (A.loop)
+                        loop_control_step(A.loop, (cudaGraphConditionalHandle)A.loop_handle, A.loop_atol,
+                                          A.loop_max_iters);
                 }
             }
         }

@@ -557,26 +557,7 @@ namespace pm {
 // condition of the graph (1: run the scan and another iteration; 0: stop).
 __global__ void loop_ctl_kernel(CtlBlock *c, cudaGraphConditionalHandle h, double atol,
                                 int max_iters) {
-    EvalStats &s = c->stats[0];
-    EvalStats &keep = c->stats[1];
-    keep.err = s.err;
-    keep.rmax = s.rmax;
-    keep.min_margin = s.min_margin;
-    keep.accepts = s.accepts;
-    const bool conv = ord_decode(s.err) <= atol;
-    if (c->nonfinite_input || conv || c->iter >= max_iters || c->scan.timeout) {
-        c->converged = conv && !c->nonfinite_input;
-        c->skip = 1;
-        cudaGraphSetConditional(h, 0);
-    } else {
-        c->iter += 1;
-        c->skip = 0;
-        s.err = kOrdNegInf;
-        s.rmax = 0x8000000000000000ull;
-        s.min_margin = 0xfff0000000000000ull;
-        s.accepts = 0;
-        cudaGraphSetConditional(h, 1);
-    }
+    loop_control_step(c, h, atol, max_iters);
 }
 
 // Fused update: the iterate of Newton iteration k lives in s_out for even k and in s_alt for
@@ -635,13 +616,21 @@ static pmcmc_status build_loop_graph(pmcmc_ctx *c, const std::string &key, const
         if (ok) {
             const bool f64 = o->precision == PMCMC_F64;
             cudaError_t e = cudaSuccess;
-            if (tg->kind == PMCMC_LOGREG) {
-                e = launch_eval_logreg(A, cs);
-                if (e == cudaSuccess && o->jac == PMCMC_JAC_DENSE) e = launch_logreg_dense_jac(A, cs);
-            } else {
-                e = launch_eval_small(A, cs);
+            // fused path: the evaluate kernel's last tile also controls the loop
+            EvalArgs Ag = A;
+            if (p.fused) {
+                Ag.loop = c->ctl;
+                Ag.loop_handle = (unsigned long long)h;
+                Ag.loop_atol = o->atol;
+                Ag.loop_max_iters = max_iters;
             }
-            if (e == cudaSuccess) {
+            if (tg->kind == PMCMC_LOGREG) {
+                e = launch_eval_logreg(Ag, cs);
+                if (e == cudaSuccess && o->jac == PMCMC_JAC_DENSE) e = launch_logreg_dense_jac(Ag, cs);
+            } else {
+                e = launch_eval_small(Ag, cs);
+            }
+            if (e == cudaSuccess && !p.fused) {
                 loop_ctl_kernel<<<1, 1, 0, cs>>>(c->ctl, h, o->atol, max_iters);
                 e = cudaGetLastError();
             }

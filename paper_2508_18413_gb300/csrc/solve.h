@@ -31,6 +31,34 @@ struct CtlBlock {
     unsigned long long inner_max;
 };
 
+// One step of the device-side control of the Newton loop (Algorithm 1): decides convergence from
+// the residual statistics of the evaluation just finished, keeps them for the host, and sets
+// the WHILE condition of the graph (1: another iteration; 0: stop).  Called by a one-thread
+// kernel after the evaluate pass, or by the last tile of the fused evaluate-and-update kernel.
+__device__ inline void loop_control_step(CtlBlock *c, cudaGraphConditionalHandle h, double atol,
+                                         int max_iters) {
+    EvalStats &s = c->stats[0];
+    EvalStats &keep = c->stats[1];
+    keep.err = s.err;
+    keep.rmax = s.rmax;
+    keep.min_margin = s.min_margin;
+    keep.accepts = s.accepts;
+    const bool conv = ord_decode(s.err) <= atol;
+    if (c->nonfinite_input || conv || c->iter >= max_iters || c->scan.timeout) {
+        c->converged = conv && !c->nonfinite_input;
+        c->skip = 1;
+        cudaGraphSetConditional(h, 0);
+    } else {
+        c->iter += 1;
+        c->skip = 0;
+        s.err = kOrdNegInf;
+        s.rmax = 0x8000000000000000ull;
+        s.min_margin = 0xfff0000000000000ull;
+        s.accepts = 0;
+        cudaGraphSetConditional(h, 1);
+    }
+}
+
 // Bump allocator over the context workspace (offsets, 256-byte aligned).
 struct Carve {
     size_t used = 0;
