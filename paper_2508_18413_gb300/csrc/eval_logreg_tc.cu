@@ -158,13 +158,32 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
     lo += err;
 }
 
+// The hardware approximations of 2^x, 1/x and log2 x (PTX ex2/rcp/lg2 .approx.ftz: one
+// special-function instruction each; relative error about 2^-22, subnormals flushed to zero,
+// which the callers tolerate: e^-|z| below 2^-126 only rounds 1 + e^-|z| to 1).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ln(p) for p >= 1: the binary exponent is taken exactly and only the mantissa in [1, 2) goes
 // through the hardware log2 (absolute error about 2^-22 there)
 __device__ __forceinline__ float log_of_product(float p) {
     const int b = __float_as_int(p);
     const float e = (float)((b >> 23) - 127);
     const float mant = __int_as_float((b & 0x007fffff) | 0x3f800000);
-    return (e + __log2f(mant)) * 0.69314718055994531f;
+    return (e + lg2_approx(mant)) * 0.69314718055994531f;
 }
 
 template <typename S_>
@@ -416,9 +435,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
 #pragma unroll
                 for (int i = 0; i < kCols; i++) {
                     const float zz = zcur[i];
-                    const float m = __expf(-fabsf(zz));
+                    const float m = ex2_approx(fabsf(zz) * -1.4426950408889634f);  // e^-|z|
                     const float onep = 1.0f + m;
-                    const float qv = __fdividef(1.0f, onep);
+                    const float qv = rcp_approx(onep);
                     const float mq = m * qv;
                     const bool pos = zz >= 0.0f;
                     const float p = pos ? qv : mq;   // sigmoid(z)
