@@ -14,17 +14,19 @@
 // kIdesc64); the diagonal Hessian H only shapes the Newton step and takes the single product
 // a_hi b_hi.
 //
-// Warp roles (640 threads, one CTA per SM):
-//   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one timestep per lane) and
-//              belongs to warpgroup h = w / 4, which owns columns 8h..8h+7 of every chunk and
-//              dimensions 8h..8h+7 of the state.  Z -> c = y - sigmoid(z), w = sigmoid'(z) and
-//              the log-likelihood terms; c, w are written as tf32 pairs into shared memory as
-//              the A operand of G and H.  Each warpgroup forms its dimensions of the proposal,
-//              of the residual and of J; the MH log-ratio (FP64) is summed over the four
-//              warpgroups through shared memory.
-//   warps 16-19 control, one per SM sub-partition: warp 16 allocates TMEM and issues the Z
-//              products, warp 17 issues the G and H products, lane 0 of warp 18 streams
-//              pre-swizzled design chunks with bulk copies (4 stages), warp 19 is idle.
+// Warp roles (kGroups = 2: 384 threads, one CTA per SM):
+//   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one timestep per lane) and
+//              belongs to warpgroup h = w / 4, which owns columns 16h..16h+15 of every chunk and
+//              dimensions 16h..16h+15 of the state.  Z -> c = y - sigmoid(z), w = sigmoid'(z)
+//              and the log-likelihood terms; c, w are written as tf32 pairs into shared memory
+//              as the A operand of G and H.  Each warpgroup forms its dimensions of the
+//              proposal, of the residual and of J; the MH log-ratio (FP64) is summed over the
+//              warpgroups through shared memory.  (Four warpgroups of 8 columns also compile:
+//              they issue 27% more instructions, as each warp repeats the per-chunk waits,
+//              accumulator reads and hand-offs, for about the same time.)
+//   warps 8-11 control, one per SM sub-partition: warp 8 allocates TMEM and issues the Z
+//              products, warp 9 issues the G and H products, lane 0 of warp 10 streams
+//              pre-swizzled design chunks with bulk copies (4 stages), warp 11 is idle.
 // TMEM: Z in three buffers, G per chunk in two buffers (64 columns each: the B_hi and B_lo
 // parts), H accumulated over the chunks.  The tensor core's FP32 accumulation truncates, so
 // a sum over all N rows in one accumulator would drift by up to an ulp of |G| per MMA; each
@@ -51,7 +53,7 @@ constexpr int kM = 128;                        // timesteps per CTA (MMA M; one 
 constexpr int kNB = 32;                        // design rows per chunk
 constexpr int kDP = 32;                        // padded feature dimension
 constexpr int kStages = 4;                     // chunk images in flight
-constexpr int kGroups = 4;                     // epilogue warpgroups
+constexpr int kGroups = 2;                     // epilogue warpgroups
 constexpr int kCols = kDP / kGroups;           // columns / dimensions per warpgroup: 8
 constexpr int kEpiWarps = 4 * kGroups;
 constexpr int kEpiThreads = kEpiWarps * 32;
@@ -99,7 +101,7 @@ constexpr int oLogu = oRed + kEpiWarps * 4 * 8; // double [128]: log u of each t
 // four warps of a warpgroup [4][32] (A and B), the 16 segment compositions of the earlier tiles'
 // aggregates, the tile carry [32]
 constexpr int oFw = oLogu + kM * 8;
-constexpr int oFpre = oFw + kEpiWarps * 8 * 2 * 4;
+constexpr int oFpre = oFw + kEpiWarps * kCols * 2 * 4;
 constexpr int oFseg = oFpre + 4 * 32 * 2 * 4;      // [16][32] (A, B): segment compositions
 constexpr int oFcar = oFseg + kEpiWarps * 32 * 2 * 4;
 constexpr int kSmemUsed = oFcar + 32 * 4;
@@ -117,7 +119,7 @@ __device__ __forceinline__ float post_jac(float v, float damping, int clip) {
 __device__ __forceinline__ void put_row_pair(unsigned char *hi, unsigned char *lo, int r, int h,
                                              const float (&v)[kCols]) {
 #pragma unroll
-    for (int c = 0; c < 2; c++) {
+    for (int c = 0; c < kCols / 4; c++) {
         float h4[4], l4[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
@@ -128,6 +130,15 @@ __device__ __forceinline__ void put_row_pair(unsigned char *hi, unsigned char *l
         *reinterpret_cast<float4 *>(hi + off) = make_float4(h4[0], h4[1], h4[2], h4[3]);
         *reinterpret_cast<float4 *>(lo + off) = make_float4(l4[0], l4[1], l4[2], l4[3]);
     }
+}
+
+// kCols consecutive 32-bit TMEM columns of the calling thread's lane
+static_assert(kCols == 8 || kCols == 16, "column split");
+__device__ __forceinline__ void tmem_ldc(uint32_t taddr, float (&v)[kCols]) {
+    if constexpr (kCols == 8)
+        tmem_ld8(taddr, v);
+    else
+        tmem_ld16(taddr, v);
 }
 
 // Warp-uniform bounded wait (every lane polls; every lane takes the same branch afterwards).
@@ -375,8 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         if (h == 0) reinterpret_cast<double *>(sm + oLogu)[r] = tv ? log(A.u[t]) : 0.0;
         auto add_partial = [&](int kc) {  // G of chunk kc, own dimensions
             float gp[kCols], gpl[kCols];
-            tmem_ld8(lrow + kColG + 64u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
-            tmem_ld8(lrow + kColG + 64u * (uint32_t)(kc & 1) + 32u + (uint32_t)d0, gpl);
+            tmem_ldc(lrow + kColG + 64u * (uint32_t)(kc & 1) + (uint32_t)d0, gp);
+            tmem_ldc(lrow + kColG + 64u * (uint32_t)(kc & 1) + 32u + (uint32_t)d0, gpl);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < kCols; i++) gs[i] += gp[i] + gpl[i];
@@ -393,8 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 if (ok && (ok = warp_wait(bar(bZfull + k % kZbuf), (uint32_t)(k / kZbuf) & 1u, abort_f, limit))) {
                     tc_fence_after();
                     float zl[kCols];
-                    tmem_ld8(lrow + kColZ + (uint32_t)(k % kZbuf) * 64u + (uint32_t)d0, zcur);
-                    tmem_ld8(lrow + kColZ + (uint32_t)(k % kZbuf) * 64u + 32u + (uint32_t)d0, zl);
+                    tmem_ldc(lrow + kColZ + (uint32_t)(k % kZbuf) * 64u + (uint32_t)d0, zcur);
+                    tmem_ldc(lrow + kColZ + (uint32_t)(k % kZbuf) * 64u + 32u + (uint32_t)d0, zl);
                     tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < kCols; i++) zcur[i] += zl[i];
@@ -414,17 +425,25 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 if (!(ok = warp_wait(bar(bFull + si), (uint32_t)(k / kStages) & 1u, abort_f, limit))) break;
                 tc_fence_after();
                 if (more) {
-                    tmem_ld8(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 64u + (uint32_t)d0, znext);
-                    tmem_ld8(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 64u + 32u + (uint32_t)d0, znl);
+                    tmem_ldc(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 64u + (uint32_t)d0, znext);
+                    tmem_ldc(lrow + kColZ + (uint32_t)((k + 1) % kZbuf) * 64u + 32u + (uint32_t)d0, znl);
                 }
                 const bool part2 = j >= 2;
                 if (part2) {
-                    tmem_ld8(lrow + kColG + 64u * (uint32_t)(k & 1) + (uint32_t)d0, gp);
-                    tmem_ld8(lrow + kColG + 64u * (uint32_t)(k & 1) + 32u + (uint32_t)d0, gpl);
+                    tmem_ldc(lrow + kColG + 64u * (uint32_t)(k & 1) + (uint32_t)d0, gp);
+                    tmem_ldc(lrow + kColG + 64u * (uint32_t)(k & 1) + 32u + (uint32_t)d0, gpl);
                 }
-                const float4 *ys4 = reinterpret_cast<const float4 *>(sm + oStage + si * kStageStride + 5 * kOp) + 2 * h;
-                const float4 ya = ys4[0], yb = ys4[1];
-                const float yv8[kCols] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                const float4 *ys4 =
+                    reinterpret_cast<const float4 *>(sm + oStage + si * kStageStride + 5 * kOp) + (kCols / 4) * h;
+                float yv8[kCols];  // the labels of this warpgroup's columns
+#pragma unroll
+                for (int c4 = 0; c4 < kCols / 4; c4++) {
+                    const float4 yq = ys4[c4];
+                    yv8[4 * c4] = yq.x;
+                    yv8[4 * c4 + 1] = yq.y;
+                    yv8[4 * c4 + 2] = yq.z;
+                    yv8[4 * c4 + 3] = yq.w;
+                }
                 float chi[kCols], clo[kCols], whi[kCols];
                 // The log-likelihood enters the MH ratio only as ll(x~) - ll(x), so its part
                 // sum_n y_n z_n is taken in the tail as (x~ - x) . X^T y, and here only
@@ -455,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                 else two_sum_acc(ll0h, ll0l, llc);
                 unsigned char *cw = sm + oCW + b * kCWStride;
 #pragma unroll
-                for (int c4 = 0; c4 < 2; c4++) {
+                for (int c4 = 0; c4 < kCols / 4; c4++) {
                     const uint32_t off = swz128((uint32_t)r, (uint32_t)(d0 + 4 * c4));
                     *reinterpret_cast<float4 *>(cw + off) =
                         make_float4(chi[4 * c4], chi[4 * c4 + 1], chi[4 * c4 + 2], chi[4 * c4 + 3]);
@@ -539,7 +558,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         if (h == 0) {
             int acc = 0;
             if (valid) {
-                const double ell = part[r] + part[kM + r] + part[2 * kM + r] + part[3 * kM + r];
+                double ell = part[r];
+#pragma unroll
+                for (int hg = 1; hg < kGroups; hg++) ell += part[hg * kM + r];
                 const double la = (ell < 0.0 || isnan(ell)) ? ell : 0.0;
                 const double gtl = la - reinterpret_cast<const double *>(sm + oLogu)[r];
                 acc = gtl > 0.0;
@@ -558,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
         if (want_dh && ok) {
             // diag(X^T W X) accumulated over the chunks of pass 1 (untouched by pass 2); the
             // condition is warp-uniform, as the collective TMEM load requires
-            tmem_ld8(lrow + kColH + (uint32_t)d0, dh);
+            tmem_ldc(lrow + kColH + (uint32_t)d0, dh);
             tmem_wait_ld();
         }
         const float rtolf = (float)A.rtol;
@@ -637,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
             }
             named_bar(1, kEpiThreads);
             if (tid < kDP) {  // channel tid = 8 h' + i': compose warps 4 h' .. 4 h' + 3
-                const int hh = tid >> 3, ii = tid & 7;
+                const int hh = tid / kCols, ii = tid % kCols;
                 float PA = 1.0f, PB = 0.0f;
 #pragma unroll
                 for (int qq = 0; qq < 4; qq++) {
