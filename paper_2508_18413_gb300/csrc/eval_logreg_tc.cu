@@ -209,6 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
     const bool fused = A.fs_flags != nullptr;
     const int nch = (N + kNB - 1) / kNB;
     const bool want_dh = A.jac == PMCMC_JAC_DIAG;
+    // dense Jacobian (assembled by the tensor-core J kernel): the weights sigmoid'(z) at x go to
+    // w_out (T x N, FP32), and no diagonal J is written
+    const bool want_w = A.jac == PMCMC_JAC_DENSE && A.w_out != nullptr;
     const unsigned int limit = A.spin_limit ? A.spin_limit : kDefaultSpinLimit;
     volatile int *abort_f = reinterpret_cast<volatile int *>(sm + oMisc + 4);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + oMisc);
@@ -484,6 +487,12 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                         *reinterpret_cast<float4 *>(cw + 2 * kRowOp + off) =
                             make_float4(whi[4 * c4], whi[4 * c4 + 1], whi[4 * c4 + 2], whi[4 * c4 + 3]);
                 }
+                if (kW && want_w && tv) {
+                    float *wr = static_cast<float *>(A.w_out) + (size_t)t * N + (size_t)j * kNB + d0;
+#pragma unroll
+                    for (int i = 0; i < kCols; i++)
+                        if (j * kNB + d0 + i < N) wr[i] = whi[i];
+                }
                 tmem_wait_ld();
                 if (part2) {
 #pragma unroll
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1) eval_logreg_tc_kernel(EvalArgs A)
                     if (want_dh) jv = post_jac(acc ? 1.0f + eps * (-dh[i] - inv_sp2) : 1.0f, damping, A.clip);
                     if (bout) store_as<S_, float>(bout + o, rr);
                     if (fout) fout[o] = f;
-                    if (aout) store_as<S_, float>(aout + o, jv);
+                    if (aout && !want_w) store_as<S_, float>(aout + o, jv);
                     fa[i] = jv;
                     fb[i] = rr;
                 }
@@ -825,7 +834,8 @@ __global__ void logreg_tc_pack_kernel(const float *__restrict__ X, const float *
 bool logreg_tc_supported(const EvalArgs &A) {
     return !A.f64 && A.engine == 0 && A.target == PMCMC_LOGREG && A.sampler == PMCMC_MALA && A.D >= 1 &&
            A.D <= kDP && A.N >= 1 &&
-           (A.jac == PMCMC_JAC_ZERO || (A.jac == PMCMC_JAC_DIAG && A.gate_grad == 0));
+           (A.jac == PMCMC_JAC_ZERO ||
+            ((A.jac == PMCMC_JAC_DIAG || A.jac == PMCMC_JAC_DENSE) && A.gate_grad == 0));
 }
 
 // the chunk images, then X^T y (kDP floats)

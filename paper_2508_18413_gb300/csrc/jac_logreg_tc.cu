@@ -257,8 +257,12 @@ __global__ void __launch_bounds__(kThreads, 1) jac_logreg_tc_kernel(EvalArgs A) 
                         if (!(in1 || in2)) continue;
                         const float h = -v[c] - (i == j ? inv_sp2 : 0.0f);
                         const float base = ga * eps * h + (i == j ? 1.0f : 0.0f);
-                        if (in1) stg[(eij - e0) * 33 + lane] = post_jac(base + ru[i] * rv[j], damping, A.clip);
-                        if (in2) stg[(eji - e0) * 33 + lane] = post_jac(base + ru[j] * rv[i], damping, A.clip);
+                        // the gate term u_t v_t^T is zero with the gate held (its vectors are
+                        // then not written)
+                        const float gij = A.gate_grad ? ru[i] * rv[j] : 0.0f;
+                        const float gji = A.gate_grad ? ru[j] * rv[i] : 0.0f;
+                        if (in1) stg[(eij - e0) * 33 + lane] = post_jac(base + gij, damping, A.clip);
+                        if (in2) stg[(eji - e0) * 33 + lane] = post_jac(base + gji, damping, A.clip);
                     }
                 }
                 __syncwarp();
@@ -300,7 +304,7 @@ cudaError_t launch_logreg_pair_pack(const void *X, int N, int D, void *img, cuda
 
 cudaError_t launch_jac_logreg_tc(const EvalArgs &A, cudaStream_t st) {
     if (!A.pair_img || reinterpret_cast<uintptr_t>(A.pair_img) % 16 != 0 || !A.w_out || !A.a_out ||
-        !A.acc_out || !A.rank1_u || !A.rank1_v)
+        !A.acc_out || (A.gate_grad && (!A.rank1_u || !A.rank1_v)))
         return cudaErrorInvalidValue;
     if (A.T <= 0) return cudaSuccess;
     cudaError_t e = ensure_dyn_smem(jac_logreg_tc_kernel, kSmemBytes);

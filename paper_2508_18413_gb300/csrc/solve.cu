@@ -441,7 +441,7 @@ struct Plan {
 // pair variant keeps the separate scan, which is what stores the pairs in bfloat16).
 // PMCMC_FUSED_UPDATE=0 selects the separate scan (measurements).
 static bool fused_update(bool tc, const pmcmc_options *o) {
-    if (!tc || o->precision != PMCMC_F32) return false;
+    if (!tc || o->precision != PMCMC_F32 || o->jac == PMCMC_JAC_DENSE) return false;
     const char *e = getenv("PMCMC_FUSED_UPDATE");
     return !(e && e[0] == '0');
 }

@@ -2,8 +2,10 @@
 per term): H_t = X^T W_t X over the pairs i <= j as one GEMM per 128-timestep tile, the pairs
 split over CTAs of up to 256 columns (D = 22: one group, 25: two, 32: three).
 
-Bars.  Against the CUDA-core FP32 assembly of the same linearisation (same evaluate pass, so the
-same accept decisions and gate vectors): a rejected step's J carries no H term and must agree
+Bars.  Against the CUDA-core FP32 assembly of the same linearisation (with the gate term the
+evaluate pass is the CUDA-core one on both sides; with the gate held the tensor-core evaluate
+pass feeds the tensor-core J, so f is held to the FP32 bar and steps within 1e-4 of a tie are
+left out): a rejected step's J carries no H term and must agree
 to FP32 rounding; an accepted step's J differs by eps times the tf32 error of the H entries,
 which is at most 2^-10 (w truncated by the tensor core) + 2^-11 (Y rounded) relative per term,
 so |dJ_ij| <= eps * 2e-3 * sum_n w_tn |X_ni X_nj| + 1e-5 (1 + |J_ij|).  Against the FP64
@@ -53,28 +55,36 @@ def test_tc_dense_jacobian_matches_cuda_cores_and_oracle(D, N, T, gate):
     eps = 0.02 if N < 1000 else 0.002
     f, J, acc = _linearize(gt, D, T, s0, s, xi, u, eps, gate, "auto")
     f2, J2, acc2 = _linearize(gt, D, T, s0, s, xi, u, eps, gate, "simt")
-    assert np.array_equal(acc, acc2)
-    np.testing.assert_array_equal(f, f2)
-    # tf32 bound of the H term, per entry
     prev = np.vstack([s0[None, :], s[:-1]])
-    z = prev @ X32.T
+    p = O.Problem(ot, "mala", eps, xi=xi, u=u, gate_grad=gate)
+    logu = np.log(u)
+    margin = np.array([abs(min(0.0, O.f(p, t + 1, prev[t])[1]) - logu[t]) for t in range(T)])
+    if gate:  # the same CUDA-core evaluate pass on both sides
+        assert np.array_equal(acc, acc2)
+        np.testing.assert_array_equal(f, f2)
+        keep = np.ones(T, dtype=bool)
+    else:  # "auto" evaluates on the tensor cores (split tf32) as well: FP32 bar, near-ties aside
+        keep = margin >= 1e-4
+        assert np.array_equal(acc[keep], acc2[keep])
+        np.testing.assert_allclose(f[keep], f2[keep], rtol=2e-5, atol=2e-5)
+    J, J2, acc = J[keep], J2[keep], acc[keep]
+    # tf32 bound of the H term, per entry
+    z = prev[keep] @ X32.T
     sg = 1.0 / (1.0 + np.exp(-z))
     w = sg * (1.0 - sg)
     absxx = np.abs(np.einsum("ni,nj->nij", X32, X32)).reshape(N, D * D)
-    bound = (eps * 2e-3 * (w @ absxx)).reshape(T, D, D) * acc[:, None, None]
+    bound = (eps * 2e-3 * (w @ absxx)).reshape(-1, D, D) * acc[:, None, None]
     bound += 1e-5 * (1.0 + np.abs(J2))
     err = np.abs(J - J2)
     assert (err <= bound).all(), (err.max(), np.unravel_index((err - bound).argmax(), err.shape))
     # the oracle's Jacobian at the same states, where the decision is not a near-tie
-    p = O.Problem(ot, "mala", eps, xi=xi, u=u, gate_grad=gate)
-    logu = np.log(u)
+    idx = np.nonzero(keep)[0]
     checked = 0
-    for t in range(0, T, max(1, T // 40)):
+    for m in range(0, len(idx), max(1, len(idx) // 40)):
+        t = idx[m]
         fo, ello, acco = O.f(p, t + 1, prev[t])
-        if abs(min(0.0, ello) - logu[t]) < 1e-4:
-            continue
-        assert acc[t] == acco
-        np.testing.assert_allclose(J[t], O.jacobian(p, t + 1, prev[t], "dense"), rtol=2e-3, atol=2e-3)
+        assert acc[m] == acco
+        np.testing.assert_allclose(J[m], O.jacobian(p, t + 1, prev[t], "dense"), rtol=2e-3, atol=2e-3)
         checked += 1
     assert checked >= 1
 
