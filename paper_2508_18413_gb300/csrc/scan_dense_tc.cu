@@ -375,9 +375,10 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
 
 }  // namespace
 
-// chunk length: the tiles of one wave of two CTAs per SM (152 SMs) share the timesteps, so the
-// serial chain of each tile is as short as that allows; 8 to 64 timesteps
-int dense_tc_chunk(int T) { return std::min(64, std::max(8, ceil_div(T, kNChunk * 2 * 152))); }
+// chunk length: the tiles of one wave (one CTA per SM, 152 SMs: the occupancy this kernel gets)
+// share the timesteps, so the serial chain of each tile is as short as one wave allows; 8 to
+// 256 timesteps (beyond 4 x 152 x 256 timesteps the tiles take several waves)
+int dense_tc_chunk(int T) { return std::min(256, std::max(8, ceil_div(T, kNChunk * 152))); }
 
 template <typename SA, typename SB>
 static cudaError_t run_dense_tc(int T, int D, int C, const void *a, const void *b, void *s,

@@ -115,8 +115,8 @@ def test_dense_tc_scan_contracting(D):
     want = O.linear_recursion(a32, b32, dense=True)
     err = np.abs(out - want) / (1 + np.abs(want))
     assert err.max() <= 5e-2, err.max()
-    # the kernel's chunk length: ceil(T / (4 chunks x 2 CTAs x 152 SMs)), clamped to [8, 64]
-    model = _chunk_model(a32, b32, min(64, max(8, -(-T // (4 * 2 * 152)))))
+    # the kernel's chunk length: ceil(T / (4 chunks x 152 SMs)), clamped to [8, 256]
+    model = _chunk_model(a32, b32, min(256, max(8, -(-T // (4 * 152)))))
     err_model = np.abs(model - want) / (1 + np.abs(want))
     assert err.max() <= 1.5 * err_model.max() and err.mean() <= 1.5 * err_model.mean(), \
         (err.max(), err_model.max(), err.mean(), err_model.mean())
