@@ -5,8 +5,9 @@
 // vectors u_t, v_t written by the evaluate pass.  The entries of X^T W_t X over the pairs
 // (i <= j) are, for a tile of 128 timesteps, one GEMM against a pair image of the design:
 //   S[t, p] = sum_n w_tn Y_np,   Y_np = X_ni X_nj,
-// with M = 128 timesteps (one TMEM lane each), N = the pairs of this CTA's group (up to 256
-// columns: the P = D (D + 1) / 2 pairs are split over ceil(P / 256) CTAs), K = the data rows in
+// with M = 128 timesteps (one TMEM lane each), N = the pairs of this CTA's group (up to 512
+// columns in MMA blocks of up to 256: the P = D (D + 1) / 2 pairs are split over ceil(P / 512)
+// CTAs, one for D <= 31), K = the data rows in
 // chunks of 32 (tcgen05.mma kind::tf32, one product per term).  One tf32 product suffices:
 // J only shapes the Newton step (any J leads to the same fixed point), and 2^-11 relative per
 // term keeps J within 1e-3 of its FP32 value.
@@ -29,11 +30,14 @@ using namespace tc;
 
 constexpr int kM = 128;                       // timesteps per tile
 constexpr int kNB = 32;                       // data rows per chunk (K)
-constexpr int kGroupCols = 256;               // pairs per CTA at most (MMA N)
+// pairs per CTA at most: two MMA column blocks of up to 256 (one 512-column TMEM allocation),
+// so one CTA takes all pairs of a tile for D <= 31 and the grid is one wave of tiles
+constexpr int kGroupCols = 512;
+constexpr int kMmaCols = 256;                 // MMA N per column block
 constexpr int kThreads = 160;
 constexpr int kIss = 4;                       // issuer warp
 constexpr int kAOp = kM * kNB * 4;            // A stage: 128 x 32 floats = 16 KB
-constexpr int kBOp = kGroupCols * kNB * 4;    // B stage: up to 256 x 32 floats = 32 KB
+constexpr int kBOp = kGroupCols * kNB * 4;    // B stage: up to 512 x 32 floats = 64 KB
 constexpr int kStages = 2;
 constexpr int oA = 0;
 constexpr int oB = kStages * kAOp;
@@ -107,10 +111,10 @@ __global__ void __launch_bounds__(kThreads, 1) jac_logreg_tc_kernel(EvalArgs A) 
     const unsigned int limit = A.spin_limit ? A.spin_limit : kDefaultSpinLimit;
     volatile int *abort_f = reinterpret_cast<volatile int *>(sm + oMisc + 4);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + oMisc);
-    unsigned char *pij = sm + oPairs;  // [0..255]: i, [256..511]: j
+    unsigned char *pij = sm + oPairs;  // [0, kGroupCols): i, [kGroupCols, 2 kGroupCols): j
     unsigned char *own = sm + oOwn;
     auto bar = [&](int i) -> uint32_t { return sb + oBar + 8u * (uint32_t)i; };
-    const uint32_t tcols = ncol <= 32 ? 32u : ncol <= 64 ? 64u : ncol <= 128 ? 128u : 256u;
+    const uint32_t tcols = ncol <= 32 ? 32u : ncol <= 64 ? 64u : ncol <= 128 ? 128u : ncol <= 256 ? 256u : 512u;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) {
@@ -151,7 +155,10 @@ __global__ void __launch_bounds__(kThreads, 1) jac_logreg_tc_kernel(EvalArgs A) 
 
     if (warp == kIss) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(kM, ncol);
+            // column blocks: [0, 256) and [256, ncol), each a multiple of 16
+            const int nblk = ncol > kMmaCols ? 2 : 1;
+            const uint32_t idesc0 = idesc_tf32(kM, ncol > kMmaCols ? kMmaCols : ncol);
+            const uint32_t idesc1 = idesc_tf32(kM, ncol > kMmaCols ? ncol - kMmaCols : 16);
             int ncopy = 0, nmma = 0;
             bool ok = true;
             auto copy = [&](int k) {
@@ -168,9 +175,13 @@ __global__ void __launch_bounds__(kThreads, 1) jac_logreg_tc_kernel(EvalArgs A) 
                 if (!(ok = mbar_wait(bar(bAready + s), par, abort_f, limit))) break;
                 tc_fence_after();
 #pragma unroll
-                for (int kk = 0; kk < kNB / 8; kk++)
-                    mma_tf32(tm, sdesc(sb + oA + s * kAOp + 32 * kk), sdesc(sb + oB + s * kBOp + 32 * kk), idesc,
-                             (k > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < kNB / 8; kk++) {
+                    const uint64_t ad = sdesc(sb + oA + s * kAOp + 32 * kk);
+                    mma_tf32(tm, ad, sdesc(sb + oB + s * kBOp + 32 * kk), idesc0, (k > 0 || kk > 0) ? 1u : 0u);
+                    if (nblk > 1)  // rows 256.. of the B stage: 256 rows x 128 bytes further on
+                        mma_tf32(tm + (uint32_t)kMmaCols, ad, sdesc(sb + oB + s * kBOp + kMmaCols * 128 + 32 * kk),
+                                 idesc1, (k > 0 || kk > 0) ? 1u : 0u);
+                }
                 mma_commit(bar(bEmpty + s));
                 nmma++;
                 if (k + kStages < nch) {  // this stage's MMAs read B: wait for them before the refill

@@ -1,6 +1,7 @@
 """Dense logistic-MALA Jacobian assembled on the tensor cores (tcgen05 kind::tf32, one product
 per term): H_t = X^T W_t X over the pairs i <= j as one GEMM per 128-timestep tile, the pairs
-split over CTAs of up to 256 columns (D = 22: one group, 25: two, 32: three).
+split over CTAs of up to 512 columns in MMA blocks of up to 256 (D = 22: one block, 25: two
+blocks, 32: two CTAs).
 
 Bars.  Against the CUDA-core FP32 assembly of the same linearisation (with the gate term the
 evaluate pass is the CUDA-core one on both sides; with the gate held the tensor-core evaluate
