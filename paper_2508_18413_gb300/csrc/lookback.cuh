@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace pm {
 
@@ -122,27 +123,30 @@ __device__ void lookback_block64(const unsigned int *flags, const R *gagg, const
     }
 }
 
-// Shared-memory values per aggregate staged by lookback_dense: D rows of D + 1 (padded) and b.
-__host__ __device__ constexpr int dense_stage_stride(int D) { return D * (D + 1) + D; }
+// Stride of a tile's aggregate (A row-major, then b: D * D + D values) in the dense look-back's
+// aggregate array, rounded up to a multiple of 4 values so that every aggregate starts on a
+// 16-byte boundary and a run of them is one bulk copy.
+__host__ __device__ constexpr int dense_agg_stride(int D) { return (D * D + D + 3) & ~3; }
 
-// Dense look-back (D <= 32; tile aggregates are affine maps (A, b), A row-major, D * D + D
-// values per tile in gagg; inclusive values D per tile in gincl).  Warp 0 finds the nearest
-// predecessor with a published inclusive value, 32 flags per round (a ballot picks the nearest
-// lane that saw an inclusive flag or ran past tile 0).  The aggregates of the tiles in between
-// are then staged into shared memory `stage` (nb of them at a time, dense_stage_stride(D)
-// values each; all threads load, each a whole row, rows padded to D + 1 so that lane r reading
-// row r is free of bank conflicts) and warp 0 applies them in order as matrix-vector products,
-// the vector held one component per lane.  A timed-out wait (recorded in ctl) leaves a zero
-// carry.  The carry of component d ends in carry_out[d].  Called by all threads of the block
-// (NT of them, Bar their barrier).
-template <typename R, int NT, class Bar = CtaBar>
+// Dense look-back (D <= 32; tile aggregates are affine maps (A, b) stored at dense_agg_stride(D)
+// values per tile in gagg; inclusive values D per tile in gincl), run by warp 0 of the block.
+// The warp finds the nearest predecessor with a published inclusive value, 32 flags per round
+// (a ballot picks the nearest lane that saw an inclusive flag or ran past tile 0).  The
+// aggregates of the tiles in between are a contiguous run of gagg: lane 0 stages it into shared
+// memory by bulk copies (cp.async.bulk, completing on the two mbarriers at bars, bars + 8) in
+// batches of up to nb aggregates, double-buffered so that the next batch is in flight while the
+// warp applies the current one as matrix-vector products (the vector held one component per
+// lane).  Lane r reads row r of A starting at column r and wrapping around, so at D = 32 the 32
+// lanes read 32 different banks.  A wait that runs out (recorded in ctl) leaves a zero carry;
+// copies in flight are drained before return.  The carry of component d ends in carry_out[d].
+// Called by all threads of the block (Bar their barrier); stage holds 2 nb aggregates.
+template <typename R, class Bar = CtaBar>
 __device__ void lookback_dense(const unsigned int *flags, const R *gagg, const R *gincl, int tile,
                                int D, unsigned int epoch, unsigned int spin_limit, ScanCtl *ctl,
-                               R *stage, int nb, R *carry_out) {
-    __shared__ int s_jj;
+                               R *stage, int nb, uint32_t bars, R *carry_out) {
+    static_assert(sizeof(R) == 4, "four-byte values");
     const int tid = threadIdx.x, lane = tid & 31;
-    const int DD = D * D, SQ = dense_stage_stride(D);
-    const size_t AGG = (size_t)DD + D;
+    const int DD = D * D, AS = dense_agg_stride(D);
     if (tid < 32) {
         int jend = tile - 1, jj = -1;
         bool timed_out = false;
@@ -160,43 +164,77 @@ __device__ void lookback_dense(const unsigned int *flags, const R *gagg, const R
             }
             jend -= 32;
         }
-        if (lane == 0) s_jj = timed_out ? -2 : jj;
-    }
-    Bar::sync();
-    const int jj = s_jj;
-    R v = R(0);  // warp 0: component `lane` of the running vector
-    if (tid < 32 && jj >= 0 && lane < D) v = __ldcg(gincl + (size_t)jj * D + lane);
-    for (int m0 = (jj == -2 ? tile : jj + 1); m0 < tile; m0 += nb) {
-        const int cnt = min(nb, tile - m0);
-        // stage rows: (aggregate q, row r), r == D is b
-        for (int idx = tid; idx < cnt * (D + 1); idx += NT) {
-            const int q = idx / (D + 1), r = idx - q * (D + 1);
-            const R *src = gagg + (size_t)(m0 + q) * AGG + (size_t)r * D;
-            R *dst = stage + (size_t)q * SQ + r * (D + 1);
-            R tmp[32];
-#pragma unroll
-            for (int c = 0; c < 32; c++) tmp[c] = c < D ? __ldcg(src + c) : R(0);
-#pragma unroll
-            for (int c = 0; c < 32; c++)
-                if (c < D) dst[c] = tmp[c];
+        R v = R(0);  // component `lane` of the running vector
+        if (!timed_out && jj >= 0 && lane < D) v = __ldcg(gincl + (size_t)jj * D + lane);
+        const int m0 = timed_out ? tile : jj + 1;
+        const uint32_t sbase = tc::smem_u32(stage);
+        // the flags were acquired by the warp's lanes: order them before lane 0's copies, and
+        // the aggregates they publish (generic stores) before the copies' reads (async proxy)
+        // (one fence covers every copy: all the aggregates they read were published before the
+        // flags the walk observed)
+        __syncwarp();
+        if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+        auto issue = [&](int buf, int m) {  // lane 0: aggregates m .. m + cnt - 1 into buffer buf
+            const int cnt = min(nb, tile - m);
+            const uint32_t bytes = (uint32_t)(cnt * AS * (int)sizeof(R));
+            tc::mbar_arrive_expect_tx(bars + 8u * (uint32_t)buf, bytes);
+            tc::bulk_g2s(sbase + (uint32_t)(buf * nb * AS * (int)sizeof(R)), gagg + (size_t)m * AS, bytes,
+                         bars + 8u * (uint32_t)buf);
+        };
+        int issued = 0, waited = 0;
+        if (m0 < tile) {
+            if (lane == 0) issue(0, m0);
+            issued = 1;
         }
-        Bar::sync();
-        if (tid < 32) {
-            for (int q = 0; q < cnt; q++) {
-                const R *Aq = stage + (size_t)q * SQ;
-                R acc0 = lane < D ? Aq[D * (D + 1) + lane] : R(0), acc1 = R(0);
-#pragma unroll
-                for (int k = 0; k < 32; k += 2) {
-                    const R v0 = __shfl_sync(0xffffffffu, v, k), v1 = __shfl_sync(0xffffffffu, v, k + 1);
-                    if (k < D && lane < D) acc0 = fma(Aq[lane * (D + 1) + k], v0, acc0);
-                    if (k + 1 < D && lane < D) acc1 = fma(Aq[lane * (D + 1) + k + 1], v1, acc1);
+        bool ok = true;
+        for (int m = m0, b = 0; m < tile && ok; b++) {
+            const int buf = b & 1, cnt = min(nb, tile - m), mn = m + cnt;
+            if (mn < tile) {  // the other buffer was last read in batch b - 1, finished by the warp
+                if (lane == 0) {
+                    tc::fence_async_smem();
+                    issue(buf ^ 1, mn);
                 }
-                v = lane < D ? acc0 + acc1 : R(0);
+                issued++;
             }
+            Spin spin(spin_limit);
+            while (!tc::mbar_try_wait(bars + 8u * (uint32_t)buf, (uint32_t)(b >> 1) & 1u))
+                if (!spin.again()) {
+                    ok = false;
+                    break;
+                }
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) atomicExch(&ctl->timeout, 1u);
+                v = R(0);
+                break;
+            }
+            waited++;
+            const R *stg = stage + (size_t)buf * nb * AS;
+            for (int q = 0; q < cnt; q++) {
+                const R *Aq = stg + (size_t)q * AS;
+                R acc[2] = {lane < D ? Aq[DD + lane] : R(0), R(0)};
+                const R *Ar = Aq + (lane < D ? lane : 0) * D;
+#pragma unroll
+                for (int k = 0; k < 32; k++) {  // column (lane + k) mod D
+                    int c = lane + k;
+                    c = c >= D ? c - D : c;
+                    c = c < 32 ? c : 0;
+                    const R vk = __shfl_sync(0xffffffffu, v, c);
+                    if (k < D && lane < D) acc[k & 1] = fma(Ar[c], vk, acc[k & 1]);
+                }
+                v = lane < D ? acc[0] + acc[1] : R(0);
+            }
+            __syncwarp();
+            m = mn;
         }
-        Bar::sync();
+        // copies issued but not waited for (after a timeout): let them land before the buffers
+        // are reused or the block exits
+        if (lane == 0)
+            for (int b = waited; b < issued; b++)
+                tc::mbar_wait_drain(bars + 8u * (uint32_t)(b & 1), (uint32_t)(b >> 1) & 1u, 1u << 20);
+        __syncwarp();
+        if (lane < D) carry_out[lane] = v;
     }
-    if (tid < D) carry_out[tid] = v;
     Bar::sync();
 }
 

@@ -45,7 +45,7 @@ constexpr int oTA = oBv + 2 * kNChunk * 32 * 4;        // tile aggregate A [32][
 constexpr int oTmp = oTA + 32 * kPStride * 4;          // product scratch [32][33]
 constexpr int oVec = oTmp + 32 * kPStride * 4;         // vectors [8][32]
 constexpr int oBar = (oVec + 8 * 32 * 4 + 7) & ~7;
-constexpr int kNBar = 3;                               // A ready (x2), MMA done
+constexpr int kNBar = 5;                               // A ready (x2), MMA done, look-back copies (x2)
 constexpr int oMisc = oBar + 8 * kNBar;
 constexpr int kSmemUsed = oMisc + 32;
 constexpr int kSmemBytes = kSmemUsed + 1024;
@@ -104,7 +104,7 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
     const uint32_t sb = smem_u32(sm);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int DD = D * D;
-    const size_t AGG = (size_t)DD + D;
+    const size_t AGG = (size_t)dense_agg_stride(D);  // 16-byte aligned aggregates
     const unsigned int limit = spin_limit ? spin_limit : kDefaultSpinLimit;
     volatile int *abort_f = reinterpret_cast<volatile int *>(sm + oMisc + 4);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + oMisc);
@@ -119,6 +119,8 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
         mbar_init(bar(0), kEpi);
         mbar_init(bar(1), kEpi);
         mbar_init(bar(2), 1);
+        mbar_init(bar(3), 1);
+        mbar_init(bar(4), 1);
         *abort_f = 0;
         tile_slot[0] = atomicAdd(&ctl->ticket, 1u);
         tile_slot[1] = *(volatile unsigned int *)&ctl->epoch;
@@ -283,11 +285,12 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
     if (tid < kP) carry[tid] = 0.0f;
     __syncthreads();
     if (tile > 0) {
-        // the A and B operand buffers are free after phase A: they stage the aggregates
+        // the A and B operand buffers are free after phase A: they stage the aggregates, two
+        // batches of nb
         constexpr int kStageBytes = 2 * kABuf + 2 * kBRegion;
-        const int nb = min(32, kStageBytes / (int)(sizeof(float) * dense_stage_stride(D)));
-        lookback_dense<float, kThreads>(flags, gagg, gincl, tile, D, epoch, limit, ctl,
-                                        reinterpret_cast<float *>(sm + oA), nb, carry);
+        const int nb = min(32, kStageBytes / (2 * (int)sizeof(float) * dense_agg_stride(D)));
+        lookback_dense<float>(flags, gagg, gincl, tile, D, epoch, limit, ctl,
+                              reinterpret_cast<float *>(sm + oA), nb, bar(3), carry);
         if (tid < D) {  // inclusive value of this tile = TA carry + tb
             float acc = vec[tid];
             for (int k = 0; k < D; k++) acc = fmaf(TA[tid * kPStride + k], carry[k], acc);
