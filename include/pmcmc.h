@@ -131,8 +131,11 @@ typedef struct {
     unsigned int chain_id;   /* noise counter of this chain */
     int spin_limit;       /* look-back wait bound (polls); 0 = default */
     int engine;           /* 0: automatic (tensor cores where a kernel exists: MALA on LOGREG,
-                             F32, D <= 32, DIAG with gate_grad 0 or ZERO; the adjoint's dense
-                             Jacobians on LOGREG, F32, 64 < D <= 128); 1: CUDA cores only */
+                             F32, D <= 32, DIAG or DENSE with gate_grad 0, or ZERO, for the
+                             evaluate pass; the DENSE Jacobian of MALA on LOGREG, F32, D <= 32;
+                             the adjoint's dense Jacobians on LOGREG, F32, 64 < D <= 128);
+                             1: CUDA cores only.  The dense scan of F32_SCAN_BF16 composes on
+                             the tensor cores either way. */
     int seq_after;        /* pmcmc_solve_batched: 0 = off; > 0 = a chain not converged after
                              this many Newton sweeps is completed by the sequential loop */
     int window;           /* pmcmc_solve: 0 = off; W > 0 = sliding-window updates (Section 3.4):
