@@ -39,6 +39,13 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st);
 
+// Diagonal scan on thread-block clusters (FP32 iterates, D <= 32, a, b and s 16-byte aligned;
+// storage 1: a and b bfloat16).
+int diag_scan_tile_cluster(int D, int sbytes);
+cudaError_t launch_scan_diag_cluster(int storage, int T, int D, const void *a, const void *b, void *s,
+                                     const void *s_reset, const ScanWork &w, EvalStats *stats,
+                                     const int *skip, unsigned int spin_limit, cudaStream_t st);
+
 // Dense scan with the compositions on the tensor cores (bfloat16 products, FP32 accumulation),
 // 4 < D <= 32: b bfloat16; a bfloat16 (a_bf16) or float.  Tiles of 4 chunks of `chunk` steps.
 int dense_tc_chunk(int T);

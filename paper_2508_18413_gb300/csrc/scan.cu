@@ -21,6 +21,7 @@
 #include "internal.h"
 #include "tc.cuh"
 #include "lookback.cuh"
+#include "scan_util.cuh"
 
 namespace pm {
 
@@ -29,70 +30,6 @@ namespace {
 constexpr int kScanThreads = 256;
 
 __device__ __forceinline__ int smem_idx(int e) { return e + (e >> 5); }  // pad 1 word / 32
-
-__device__ __forceinline__ unsigned int take_tile(ScanCtl *ctl, unsigned int *s_tile,
-                                                  unsigned int *s_epoch) {
-    if (threadIdx.x == 0) {
-        *s_tile = atomicAdd(&ctl->ticket, 1u);
-        *s_epoch = *(volatile unsigned int *)&ctl->epoch;
-    }
-    __syncthreads();
-    return *s_tile;
-}
-
-__device__ __forceinline__ void finish_tile(ScanCtl *ctl, unsigned int ntiles) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned int d = atomicAdd(&ctl->done, 1u);
-        if (d == ntiles - 1) {  // last CTA: reset for the next launch
-            ctl->ticket = 0;
-            ctl->done = 0;
-            ctl->epoch = ctl->epoch + 1u;
-            __threadfence();
-        }
-    }
-}
-
-// Block-wide reduction of the scan statistics: one atomic per CTA (same-address atomics from
-// every warp of every tile serialise in L2).  Called by all threads of the CTA.
-__device__ __forceinline__ void block_stats(EvalStats *stats, double dmax, unsigned int resets) {
-    __shared__ double s_dm[32];
-    __shared__ unsigned int s_rs[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    double dm = warp_max(dmax);
-    unsigned int rs = warp_sum(resets);
-    if (lane == 0) {
-        s_dm[w] = dm;
-        s_rs[w] = rs;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < nw; i++) {
-            dm = fmax(dm, s_dm[i]);
-            rs += s_rs[i];
-        }
-        if (dm > 0) atomic_max_d(&stats->dmax, dm);
-        if (rs) atomicAdd(&stats->resets, (unsigned long long)rs);
-    }
-}
-
-// Exit of a persistent scan kernel: every CTA has taken its last (out-of-range) ticket before it
-// counts itself out, so the last CTA to leave can reset the ticket and advance the epoch with
-// no CTA left that could take another ticket.
-__device__ __forceinline__ void exit_persistent(ScanCtl *ctl) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int e = atomicAdd(&ctl->done, 1u);
-        if (e == gridDim.x - 1) {
-            ctl->ticket = 0;
-            ctl->done = 0;
-            ctl->epoch = ctl->epoch + 1u;
-            __threadfence();
-        }
-    }
-}
 
 }  // namespace
 
@@ -963,13 +900,15 @@ static int scan_kernel_choice(long long elems) {
     if (e && strcmp(e, "rows") == 0) return 0;
     if (e && strcmp(e, "staged") == 0) return 1;
     if (e && strcmp(e, "pipe") == 0) return 2;
+    if (e && strcmp(e, "cluster") == 0) return 3;
     return (elems > (1ll << 21) && elems <= 3ll * (1ll << 22)) ? 2 : 0;
 }
 
 int diag_scan_tile(int T, int D, int elem_bytes) {
     if (D <= 32)  // the smallest tile of the kernels that may run sizes the workspace
         return std::min({diag_scan_tile_rows(T, D), staged_tile(T, D, elem_bytes),
-                         8 * (32 / D) * pipe_run(T, D, elem_bytes, elem_bytes, 2)});
+                         8 * (32 / D) * pipe_run(T, D, elem_bytes, elem_bytes, 2),
+                         diag_scan_tile_cluster(D, 4)});
     // enough tiles to fill the GPU twice over, at most ~4096 elements (FP32) per tile
     const int max_elems = elem_bytes >= 8 ? 2048 : 4096;
     int tt_max = std::max(8, (max_elems / std::max(D, 1)) / 8 * 8);
@@ -1156,6 +1095,8 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st) {
     const int choice = D <= 32 ? scan_kernel_choice((long long)T * D) : 0;
+    if (D <= 32 && choice == 3 && !f64 && aligned16(a) && aligned16(b) && aligned16(s))
+        return launch_scan_diag_cluster(storage, T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
     if (D <= 32 && choice == 2 && aligned16(a) && aligned16(b) && aligned16(s)) {
         if (f64) return run_scan_pipe<double, double>(T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
         if (storage == 1)

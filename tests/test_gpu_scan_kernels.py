@@ -1,7 +1,9 @@
 """Every diagonal-scan kernel (D <= 32) against the oracle's plain linear recursion.
 
 The kernel is chosen per launch by PMCMC_SCAN_KERNEL (rows: the register-resident kernels,
-staged: bulk copies into shared memory, pipe: persistent and double-buffered).  Shapes span one
+staged: bulk copies into shared memory, pipe: persistent and double-buffered, cluster: tiles
+shared by a thread-block cluster, FP32 iterates only; FP64 falls back to the row kernels there,
+so those cases check the fallback).  Shapes span one
 tile to tens of tiles per CTA, ragged last tiles (including tails shorter than a 16-byte bulk
 copy), lane groups of every width 32 / D, and the non-finite reset.  Bar: FP64 to 1e-12, FP32
 (and bf16 storage, compared with the rounded a, b the kernel reads) to 2e-5 relative."""
@@ -19,15 +21,30 @@ if torch.cuda.is_available():
     import paper_2508_18413_gb300 as P
 
 DEV = "cuda:0"
-KERNELS = ["rows", "staged", "pipe", "pipe2"]
+KERNELS = ["rows", "staged", "pipe", "pipe2", "cluster", "cluster4"]
+_ENV = {  # kernel variant -> environment
+    "rows": {"PMCMC_SCAN_KERNEL": "rows"},
+    "staged": {"PMCMC_SCAN_KERNEL": "staged"},
+    "pipe": {"PMCMC_SCAN_KERNEL": "pipe", "PMCMC_PIPE_CTAS": "1"},
+    "pipe2": {"PMCMC_SCAN_KERNEL": "pipe", "PMCMC_PIPE_CTAS": "2"},
+    # clusters of 8 CTAs, 4 slots, carries 2 tiles after pass 1 (the defaults)
+    "cluster": {"PMCMC_SCAN_KERNEL": "cluster", "PMCMC_SCAN_CLUSTER": "8", "PMCMC_SCAN_SLOTS": "4",
+                "PMCMC_SCAN_LAG": "2"},
+    # clusters of 4 CTAs, 8 slots, carries 5 tiles later
+    "cluster4": {"PMCMC_SCAN_KERNEL": "cluster", "PMCMC_SCAN_CLUSTER": "4", "PMCMC_SCAN_SLOTS": "8",
+                 "PMCMC_SCAN_LAG": "5"},
+}
 
 
 @pytest.fixture
 def kernel(request):
-    """rows, staged, pipe (one CTA per SM) or pipe2 (two CTAs per SM, smaller tiles)."""
-    saved = {k: os.environ.get(k) for k in ("PMCMC_SCAN_KERNEL", "PMCMC_PIPE_CTAS")}
-    os.environ["PMCMC_SCAN_KERNEL"] = "pipe" if request.param == "pipe2" else request.param
-    os.environ["PMCMC_PIPE_CTAS"] = "2" if request.param == "pipe2" else "1"
+    """rows, staged, pipe (one CTA per SM), pipe2 (two CTAs per SM, smaller tiles), cluster or
+    cluster4 (two cluster shapes)."""
+    keys = {k for v in _ENV.values() for k in v}
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ.pop(k, None)
+    os.environ.update(_ENV[request.param])
     yield request.param
     for k, v in saved.items():
         if v is None:
