@@ -137,7 +137,8 @@ __host__ __device__ constexpr int dense_agg_stride(int D) { return (D * D + D + 
 // batches of up to nb aggregates, double-buffered so that the next batch is in flight while the
 // warp applies the current one as matrix-vector products (the vector held one component per
 // lane).  Lane r reads row r of A starting at column r and wrapping around, so at D = 32 the 32
-// lanes read 32 different banks.  A wait that runs out (recorded in ctl) leaves a zero carry;
+// lanes read 32 different banks; the rotated columns are computed once per call (with D known
+// only at run time, recomputing them per step made each product ~2.7x slower, measured).  A wait that runs out (recorded in ctl) leaves a zero carry;
 // copies in flight are drained before return.  The carry of component d ends in carry_out[d].
 // Called by all threads of the block (Bar their barrier); stage holds 2 nb aggregates.
 template <typename R, class Bar = CtaBar>
@@ -181,6 +182,16 @@ __device__ void lookback_dense(const unsigned int *flags, const R *gagg, const R
             tc::bulk_g2s(sbase + (uint32_t)(buf * nb * AS * (int)sizeof(R)), gagg + (size_t)m * AS, bytes,
                          bars + 8u * (uint32_t)buf);
         };
+        // lane r reads row r (lanes >= D repeat row D - 1) from column r + k at step k, wrapping
+        // around: the rotated column of every step is computed once, so each product is a
+        // gather of the row into registers followed by D shuffle-multiply-adds
+        const int lr = lane < D ? lane : D - 1;
+        int cidx[32];
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            const int c = lr + k;
+            cidx[k] = c >= D ? c - D : c;
+        }
         int issued = 0, waited = 0;
         if (m0 < tile) {
             if (lane == 0) issue(0, m0);
@@ -212,17 +223,17 @@ __device__ void lookback_dense(const unsigned int *flags, const R *gagg, const R
             const R *stg = stage + (size_t)buf * nb * AS;
             for (int q = 0; q < cnt; q++) {
                 const R *Aq = stg + (size_t)q * AS;
-                R acc[2] = {lane < D ? Aq[DD + lane] : R(0), R(0)};
-                const R *Ar = Aq + (lane < D ? lane : 0) * D;
+                const R *Ar = Aq + lr * D;
+                R row[32];
 #pragma unroll
-                for (int k = 0; k < 32; k++) {  // column (lane + k) mod D
-                    int c = lane + k;
-                    c = c >= D ? c - D : c;
-                    c = c < 32 ? c : 0;
-                    const R vk = __shfl_sync(0xffffffffu, v, c);
-                    if (k < D && lane < D) acc[k & 1] = fma(Ar[c], vk, acc[k & 1]);
+                for (int k = 0; k < 32; k++) row[k] = k < D ? Ar[cidx[k]] : R(0);
+                R acc[4] = {Aq[DD + lr], R(0), R(0), R(0)};
+#pragma unroll
+                for (int k = 0; k < 32; k++) {
+                    const R vk = __shfl_sync(0xffffffffu, v, k < D ? cidx[k] : 0);
+                    if (k < D) acc[k & 3] = fma(row[k], vk, acc[k & 3]);
                 }
-                v = lane < D ? acc[0] + acc[1] : R(0);
+                v = lane < D ? (acc[0] + acc[1]) + (acc[2] + acc[3]) : R(0);
             }
             __syncwarp();
             m = mn;
