@@ -169,7 +169,7 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
         const int c = warp, r = lane;          // chunk c of the tile, row r of its matrices
         const int tc0 = t0 + c * C;            // first timestep of the chunk
         const uint32_t lrow = tm + ((uint32_t)(32 * c) << 16);
-        float jr[kP], jn[kP];
+        float jr[kP], jn[kP], jn2[kP];
         // row r of J_t (identity beyond T) and b_t[r] (zero beyond T)
         auto load_row = [&](int t, float (&v)[kP], float &bb) {
             const bool in = t < T;
@@ -179,18 +179,23 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
                                               : ((!in && k == r) ? 1.0f : 0.0f);
             bb = (in && r < D) ? ldg_as<SB, float>(b + (size_t)t * D + r) : 0.0f;
         };
-        // step 0: P_0 = J_0, b_0 = b_{t0}; the next step's row is always one step ahead
-        float bcur, bn = 0.0f;
+        // step 0: P_0 = J_0, b_0 = b_{t0}; the rows of the next two steps are always in flight
+        float bcur, bn = 0.0f, bn2 = 0.0f;
         load_row(tc0, jr, bcur);
         if (C > 1) load_row(tc0 + 1, jn, bn);
+        if (C > 2) load_row(tc0 + 2, jn2, bn2);
         bv[(0 * kNChunk + c) * 32 + r] = bcur;
 #pragma unroll
         for (int n = 0; n < kP; n++) st_bf16(sm + oB, swz_bf16((uint32_t)n, (uint32_t)(32 * c + r), kBRegion), jr[n]);
         for (int i = 1; i < C; i++) {
             float acc = bn;
 #pragma unroll
-            for (int k = 0; k < kP; k++) jr[k] = jn[k];
-            if (i + 1 < C) load_row(tc0 + i + 1, jn, bn);
+            for (int k = 0; k < kP; k++) {
+                jr[k] = jn[k];
+                jn[k] = jn2[k];
+            }
+            bn = bn2;
+            if (i + 2 < C) load_row(tc0 + i + 2, jn2, bn2);
             __syncwarp();  // b_{i-1} of every row of the chunk is in shared memory
             const float *bp = bv + (((i - 1) & 1) * kNChunk + c) * 32;
 #pragma unroll
@@ -321,23 +326,29 @@ scan_dense_tc_kernel(int T, int D, int C, const SA *__restrict__ a, const SB *__
         const int c = warp, r = lane;
         float dl = cin[c * 32 + r];
         const int tb = t0 + c * C, te = min(tb + C, T);
-        // row r of J_t, b_t[r] and s_t[r] in registers, loaded one step ahead (zeros for r >= D)
-        float jn[kP], bn = 0.0f, sv = 0.0f;
-        auto load_c = [&](int t) {
+        // row r of J_t, b_t[r] and s_t[r] in registers, loaded two steps ahead (zeros for r >= D)
+        float jn[kP], jn2[kP], bn = 0.0f, bn2 = 0.0f, sv = 0.0f, sv2 = 0.0f;
+        auto load_c = [&](int t, float (&jv)[kP], float &bb, float &ss) {
 #pragma unroll
             for (int k = 0; k < kP; k++)
-                jn[k] = (r < D && k < D) ? ldg_as<SA, float>(a + (size_t)t * DD + (size_t)r * D + k) : 0.0f;
-            bn = r < D ? ldg_as<SB, float>(b + (size_t)t * D + r) : 0.0f;
-            sv = r < D ? s[(size_t)t * D + r] : 0.0f;
+                jv[k] = (r < D && k < D) ? ldg_as<SA, float>(a + (size_t)t * DD + (size_t)r * D + k) : 0.0f;
+            bb = r < D ? ldg_as<SB, float>(b + (size_t)t * D + r) : 0.0f;
+            ss = r < D ? s[(size_t)t * D + r] : 0.0f;
         };
-        if (tb < te) load_c(tb);
+        if (tb < te) load_c(tb, jn, bn, sv);
+        if (tb + 1 < te) load_c(tb + 1, jn2, bn2, sv2);
         for (int t = tb; t < te; t++) {
             float jc[kP];
 #pragma unroll
-            for (int k = 0; k < kP; k++) jc[k] = jn[k];
+            for (int k = 0; k < kP; k++) {
+                jc[k] = jn[k];
+                jn[k] = jn2[k];
+            }
             float acc = bn;
             const float scur = sv;
-            if (t + 1 < te) load_c(t + 1);
+            bn = bn2;
+            sv = sv2;
+            if (t + 2 < te) load_c(t + 2, jn2, bn2, sv2);
 #pragma unroll
             for (int k = 0; k < kP; k++) acc = fmaf(jc[k], __shfl_sync(0xffffffffu, dl, k), acc);
             dl = r < D ? acc : 0.0f;
