@@ -1,7 +1,8 @@
 """pmcmc_scan_noalloc: the diagonal scan for callers that cannot allocate device memory (code
 running under stream capture, fixed-budget hosts, plugins under another framework's allocator).
 It must give the same result as the allocating pmcmc_scan, on consecutive calls that reuse its
-static scratch, whichever scan kernel the size (or PMCMC_SCAN_KERNEL / PMCMC_PIPE_CTAS) selects.
+static scratch, whichever scan kernel the size (or PMCMC_SCAN_KERNEL / PMCMC_PIPE_CTAS /
+PMCMC_SCAN_CLUSTER) selects.
 Collected last on purpose, so a failure here comes after every other test."""
 import os
 
@@ -65,6 +66,14 @@ def test_noalloc_scan_pipelined_two_ctas_per_sm_twice():
 @pytest.mark.gpu
 def test_noalloc_scan_staged_kernel_twice():
     _compare_twice("f32", [(200_003, 8), (150_001, 4)], env={"PMCMC_SCAN_KERNEL": "staged"})
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["f32", "f32_scan_bf16"])
+def test_noalloc_scan_cluster_kernel_twice(precision):
+    """The thread-block cluster kernel (FP32 iterates), clusters of 8 and of 4."""
+    _compare_twice(precision, [(500_009, 8), (300_007, 25)], env={"PMCMC_SCAN_KERNEL": "cluster"})
+    _compare_twice(precision, [(200_003, 3)], env={"PMCMC_SCAN_KERNEL": "cluster", "PMCMC_SCAN_CLUSTER": "4"})
 
 
 @pytest.mark.gpu
