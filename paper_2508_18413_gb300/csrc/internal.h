@@ -39,6 +39,13 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st);
 
+// Row kernel of the diagonal scan with D a compile-time constant (D a power of two up to 32,
+// 8 rows per warp, `nsub` sub-chunks per warp); kind 0: FP32, 1: FP32 with bfloat16 a and b,
+// 2: FP64.  cudaErrorInvalidValue for any other D or a tile count beyond the workspace.
+cudaError_t launch_scan_rows_dconst(int kind, int T, int D, int nsub, const void *a, const void *b, void *s,
+                                    const void *s_reset, const ScanWork &w, EvalStats *stats,
+                                    const int *skip, unsigned int spin_limit, cudaStream_t st);
+
 // Diagonal scan on thread-block clusters (FP32 iterates, D <= 32, a, b and s 16-byte aligned;
 // storage 1: a and b bfloat16).
 int diag_scan_tile_cluster(int D, int sbytes);

@@ -1,6 +1,7 @@
 """Every diagonal-scan kernel (D <= 32) against the oracle's plain linear recursion.
 
-The kernel is chosen per launch by PMCMC_SCAN_KERNEL (rows: the register-resident kernels,
+The kernel is chosen per launch by PMCMC_SCAN_KERNEL (rows: the register-resident kernels, with
+D fixed at compile time for the powers of two unless PMCMC_SCAN_DCONST=0,
 staged: bulk copies into shared memory, pipe: persistent and double-buffered, cluster: tiles
 shared by a thread-block cluster, FP32 iterates only; FP64 falls back to the row kernels there,
 so those cases check the fallback).  Shapes span one
@@ -21,9 +22,12 @@ if torch.cuda.is_available():
     import paper_2508_18413_gb300 as P
 
 DEV = "cuda:0"
-KERNELS = ["rows", "staged", "pipe", "pipe2", "cluster", "cluster4"]
+KERNELS = ["rows", "rows_generic", "staged", "pipe", "pipe2", "cluster", "cluster4"]
 _ENV = {  # kernel variant -> environment
+    # the row kernels; D a power of two runs the instance with D fixed at compile time
     "rows": {"PMCMC_SCAN_KERNEL": "rows"},
+    # the row kernels with D a run-time value for every D
+    "rows_generic": {"PMCMC_SCAN_KERNEL": "rows", "PMCMC_SCAN_DCONST": "0"},
     "staged": {"PMCMC_SCAN_KERNEL": "staged"},
     "pipe": {"PMCMC_SCAN_KERNEL": "pipe", "PMCMC_PIPE_CTAS": "1"},
     "pipe2": {"PMCMC_SCAN_KERNEL": "pipe", "PMCMC_PIPE_CTAS": "2"},
@@ -38,8 +42,8 @@ _ENV = {  # kernel variant -> environment
 
 @pytest.fixture
 def kernel(request):
-    """rows, staged, pipe (one CTA per SM), pipe2 (two CTAs per SM, smaller tiles), cluster or
-    cluster4 (two cluster shapes)."""
+    """rows, rows_generic, staged, pipe (one CTA per SM), pipe2 (two CTAs per SM, smaller
+    tiles), cluster or cluster4 (two cluster shapes)."""
     keys = {k for v in _ENV.values() for k in v}
     saved = {k: os.environ.get(k) for k in keys}
     for k in keys:
