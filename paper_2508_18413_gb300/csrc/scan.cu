@@ -806,11 +806,12 @@ static void diag_shape(int T, int D, int *rows, int *nsub) {
     }
     // measured on GB300 (2^26..2^28 elements): larger tiles amortise the fixed per-tile latency
     // (ticket, fences, look-back) up to ~32 sub-chunks, as long as the tiles still keep every
-    // SM busy several times over
+    // SM busy several times over: 32 or 16 sub-chunks with at least 8 tiles per SM, else up to
+    // 8 with at least 4 tiles per SM (at 2^24 elements 8 sub-chunks ran 4-10% faster than 4)
     const int P = 32 / D;
     *nsub = 0;
     for (int n : {32, 16, 8, 4, 2, 1})
-        if (ceil_div(T, 8 * *rows * n * P) >= 8 * 152) {
+        if (ceil_div(T, 8 * *rows * n * P) >= (n >= 16 ? 8 : 4) * 152) {
             *nsub = n;
             break;
         }
