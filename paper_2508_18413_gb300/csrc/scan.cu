@@ -731,18 +731,26 @@ static size_t pipe_smem(int M, int D, int sbytes, int rbytes) {
     return 2 * (2 * ((E * sbytes + 15) & ~(size_t)15) + ((E * rbytes + 15) & ~(size_t)15));
 }
 
-// Kernel choice for D <= 32.  By default the pipelined kernel for 2^21 < T D <= 3 * 2^22
-// elements and the register-resident kernels otherwise (measured on GB300, D = 2, 8, 25: the
-// pipelined kernel runs 1.5-2x faster in that range, where the row kernel's tiles are either
-// small or few per SM, and slower above it, where its one tile in flight per SM leaves the
-// look-back latency exposed).  PMCMC_SCAN_KERNEL=rows, staged or pipe forces a kernel (read at
-// every launch, so a process can compare them).
-static int scan_kernel_choice(long long elems) {
+// Kernel choice for D <= 32.  By default the pipelined kernel in a middle range of T D and the
+// register-resident kernels otherwise: for 2^21 < T D <= 3 * 2^22 elements in general
+// (measured on GB300, D = 2, 8, 25: the pipelined kernel runs 1.5-2x faster there than the
+// generic row kernel, whose tiles are either small or few per SM, and slower above, where its
+// one tile in flight per SM leaves the look-back latency exposed), and for 2^20 <= T D <= 2^22
+// (3 * 2^21 with bfloat16 pairs) where the row kernel has D fixed at compile time (FP32
+// iterates, D a power of two).  PMCMC_SCAN_KERNEL=rows, staged, pipe or cluster forces a kernel
+// (read at every launch, so a process can compare them).
+static int scan_kernel_choice(long long elems, int D, bool f64, int storage) {
     const char *e = getenv("PMCMC_SCAN_KERNEL");
     if (e && strcmp(e, "rows") == 0) return 0;
     if (e && strcmp(e, "staged") == 0) return 1;
     if (e && strcmp(e, "pipe") == 0) return 2;
     if (e && strcmp(e, "cluster") == 0) return 3;
+    // FP32 iterates with D a power of two, where the row kernel has D fixed at compile time
+    // (measured on GB300, D = 8: the pipelined kernel is faster from 2^20 to 2^22 elements,
+    // 3 2^21 with bfloat16 pairs; the row kernel from 3 2^21 (FP32) and 3 2^22 (bfloat16))
+    const char *dc = getenv("PMCMC_SCAN_DCONST");
+    if (!f64 && (D & (D - 1)) == 0 && !(dc && dc[0] == '0'))
+        return (elems >= (1ll << 20) && elems <= (storage == 1 ? 3ll << 21 : 1ll << 22)) ? 2 : 0;
     return (elems > (1ll << 21) && elems <= 3ll * (1ll << 22)) ? 2 : 0;
 }
 
@@ -944,7 +952,7 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
                              const void *b, void *s, const void *s_reset, const ScanWork &w,
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st) {
-    const int choice = D <= 32 ? scan_kernel_choice((long long)T * D) : 0;
+    const int choice = D <= 32 ? scan_kernel_choice((long long)T * D, D, f64, storage) : 0;
     if (D <= 32 && choice == 3 && !f64 && aligned16(a) && aligned16(b) && aligned16(s))
         return launch_scan_diag_cluster(storage, T, D, a, b, s, s_reset, w, stats, skip, spin_limit, st);
     if (D <= 32 && choice == 2 && aligned16(a) && aligned16(b) && aligned16(s)) {
