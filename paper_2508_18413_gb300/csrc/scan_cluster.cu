@@ -8,7 +8,11 @@
 // tile in shared memory, the cluster's aggregate is composed in rank 0 through distributed
 // shared memory, and one look-back per cluster tile finds its carry.  Each CTA keeps NS sub-tile
 // slots: while the look-back of tile k is in flight, its compute warps scan tile k + 1 and the
-// bulk copies of later tiles land, so neither the look-back nor the copies stall the stream.
+// bulk copies of later tiles land.  Measured on GB300 it is nevertheless slower than the row
+// kernel (28% against 49-52% of HBM at 2^26-2^28 elements): each tile's carry waits for the
+// aggregates of the tiles published in the same wave, each ~2.6 us after its cluster aggregate,
+// and four slots leave room for only two tiles between pass 1 and pass 2.  It is an option
+// (PMCMC_SCAN_KERNEL=cluster), not a default.
 //
 // Roles (480 threads per CTA):
 //   warps 0-7   compute: pass 1 (each lane group composes a run of M timesteps of one channel),
