@@ -244,6 +244,14 @@ pmcmc_status pmcmc_linearize(pmcmc_ctx *ctx, const pmcmc_target *target,
  *   D <= 32 (F32_SCAN_BF16: 4 < D <= 32, the compositions of a on the tensor cores).
  * precision: F64 (a, b, s double), F32 (float), F32_SCAN_BF16 (a, b bfloat16, s float).
  * s: T x D device, updated in place.  Single pass, decoupled look-back.
+ * The diagonal kernel (D <= 32) is chosen from T D, D and the precision; these environment
+ * variables, read at every call (comparisons, tests), override the choice: PMCMC_SCAN_KERNEL =
+ * rows | staged | pipe | cluster (cluster: FP32 and F32_SCAN_BF16 only, a, b, s 16-byte
+ * aligned, else the default); PMCMC_SCAN_SHAPE = "rows,sub-chunks" (rows 8 or 16) for the row
+ * kernel; PMCMC_SCAN_DCONST = 0 keeps the row kernel's generic instance for every D;
+ * PMCMC_PIPE_CTAS = 2 runs two pipelined CTAs per SM; PMCMC_SCAN_CLUSTER = 2 | 4 | 8,
+ * PMCMC_SCAN_SLOTS = 4 | 8 and PMCMC_SCAN_LAG shape the cluster kernel.  Results differ only by
+ * the association of the FP arithmetic.
  */
 pmcmc_status pmcmc_scan(pmcmc_ctx *ctx, pmcmc_jac kind, pmcmc_precision precision, int T, int D,
                         const void *a, const void *b, void *s, void *stream);
