@@ -246,8 +246,8 @@ pmcmc_status pmcmc_linearize(pmcmc_ctx *ctx, const pmcmc_target *target,
  * s: T x D device, updated in place.  Single pass, decoupled look-back.
  * The diagonal kernel (D <= 32) is chosen from T D, D and the precision; these environment
  * variables, read at every call (comparisons, tests), override the choice: PMCMC_SCAN_KERNEL =
- * rows | staged | pipe | cluster (cluster: FP32 and F32_SCAN_BF16 only, a, b, s 16-byte
- * aligned, else the default); PMCMC_SCAN_SHAPE = "rows,sub-chunks" (rows 8 or 16) for the row
+ * rows | staged | pipe | cluster (staged, pipe and cluster need a, b, s 16-byte aligned and
+ * cluster FP32 or F32_SCAN_BF16, else the row kernel runs); PMCMC_SCAN_SHAPE = "rows,sub-chunks" (rows 8 or 16) for the row
  * kernel; PMCMC_SCAN_DCONST = 0 keeps the row kernel's generic instance for every D;
  * PMCMC_PIPE_CTAS = 2 runs two pipelined CTAs per SM; PMCMC_SCAN_CLUSTER = 2 | 4 | 8,
  * PMCMC_SCAN_SLOTS = 4 | 8 and PMCMC_SCAN_LAG shape the cluster kernel.  Results differ only by
