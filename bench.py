@@ -339,6 +339,50 @@ def _time_fn(fn, steps, warmup, flush, stream, torch):
     return statistics.mean(ms), out
 
 
+def run_diag_scan_keys(P, torch, dev, flush, stream):
+    """The diagonal scan alone (quasi-DEER's step (b)) at 2^26 and 2^28 elements, D = 8, FP32
+    and bfloat16 pairs, with the kernel the library picks: GB/s of its algorithmic traffic (read
+    a, b, s; write s) and the fraction of the measured HBM bandwidth.  a ~ U(-0.9, 0.9),
+    b ~ N(0, 1), s ~ N(0, 1); L2 flushed before every timed scan (10 timed, 3 warm-up).  Each
+    result is checked on the first 2,048 timesteps against the recursion in FP64, and on the
+    last 2,048 against the recursion run from the scan's own value just before them (the carry
+    the look-back delivered)."""
+    D, out = 8, []
+    peak = _measured_hbm()
+    g = torch.Generator(device=dev)
+    for log2 in (26, 28):
+        for prec in ("f32", "f32_scan_bf16"):
+            T = (1 << log2) // D
+            ad = torch.bfloat16 if prec == "f32_scan_bf16" else torch.float32
+            g.manual_seed(log2)
+            a = (torch.rand((T, D), device=dev, generator=g) * 1.8 - 0.9).to(ad)
+            b = torch.randn((T, D), device=dev, generator=g).to(ad)
+            s0 = torch.randn((T, D), device=dev, generator=g)
+            s = s0.clone()
+            P.pmcmc_scan("diag", prec, a, b, s)
+            torch.cuda.synchronize()
+            w = 2048
+            d_head = (s[:w].double() - s0[:w].double()).cpu().numpy()
+            d_tail = (s[-w - 1:].double() - s0[-w - 1:].double()).cpu().numpy()
+            a_head, b_head = a[:w].double().cpu().numpy(), b[:w].double().cpu().numpy()
+            a_tail, b_tail = a[-w:].double().cpu().numpy(), b[-w:].double().cpu().numpy()
+            err = 0.0
+            for dref0, aa, bb, got in ((np.zeros(D), a_head, b_head, d_head),
+                                       (d_tail[0], a_tail, b_tail, d_tail[1:])):
+                dl = dref0.copy()
+                for t in range(w):
+                    dl = aa[t] * dl + bb[t]
+                    err = max(err, float(np.max(np.abs(got[t] - dl) / (1.0 + np.abs(dl)))))
+            ms, _ = _time_fn(lambda: P.pmcmc_scan("diag", prec, a, b, s), 10, 3, flush, stream, torch)
+            gbs = T * D * (a.element_size() + 4) * 2 / (ms / 1e3) / 1e9
+            out.append({"elements": T * D, "D": D, "precision": prec, "ms": ms, "GB/s": gbs,
+                        "frac_of_measured_hbm": gbs / peak, "max_rel_err_sampled": err})
+            del a, b, s0, s
+            torch.cuda.empty_cache()
+    return {"rows": out, "hbm_peak_measured": peak,
+            "bytes_per_element": "16 (FP32: read a, b, s; write s), 12 with bfloat16 a, b"}
+
+
 def run_configs(P, torch, dev, flush, stream):
     """C1, C3 (diagonal, bfloat16 pairs, block-quasi parallel leapfrog), the 512-chain batch and
     the Gibbs chain: samples/s of the parallel solve, its Newton iterations and the sequential
@@ -681,6 +725,13 @@ def run_ours(args):
     if rank == 0 and not args.no_variants:
         configs, keep = run_configs(P, torch, dev, flush, stream)
 
+    diag_scan = None
+    if rank == 0 and not args.no_variants:
+        try:  # an extra measurement: the headline line is printed whatever happens here
+            diag_scan = run_diag_scan_keys(P, torch, dev, flush, stream)
+        except Exception as exc:
+            diag_scan = {"error": f"{type(exc).__name__}: {exc}"}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -744,6 +795,7 @@ def run_ours(args):
             "speedup": (WL.T / (ms / 1000.0)) / (WL.T / (seq_ms / 1000.0))},
         "dense_newton": dense,
         "configs": configs,
+        "diag_scan": diag_scan,
         "parity": parity,
         "at_workload_tol_1e-5": {"value": WL.T / (statistics.mean(ms5) / 1e3), "unit": UNIT,
                                  "ms": statistics.mean(ms5), "newton_iters": res5["iters"],
