@@ -53,8 +53,8 @@ def test_noalloc_scan_matches_allocating_scan_twice(precision):
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["f32", "f32_scan_bf16"])
 def test_noalloc_scan_pipelined_kernel_twice(precision):
-    """About 4M elements at D = 8: the pipelined bulk-copy kernel (the default for
-    2^21 < T D <= 3 2^22), whose smaller tiles size the static scratch."""
+    """About 4M elements at D = 8: the pipelined bulk-copy kernel (the default there), whose
+    smaller tiles size the static scratch."""
     _compare_twice(precision, [(500_009, 8), (500_009, 8)])
 
 
