@@ -154,3 +154,29 @@ def test_row_kernel_shapes_match_linear_recursion(shape, precision, T, D):
     delta = O.linear_recursion(a_used, b_used, dense=False)
     tol = 1e-12 if precision == "f64" else 2e-5
     np.testing.assert_allclose(out - s_in, delta, rtol=tol, atol=tol * 10)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f32_scan_bf16"])
+@pytest.mark.parametrize("T,D", [((1 << 20) // 8 - 1, 8), ((1 << 20) // 8, 8), ((1 << 22) // 8, 8),
+                                 ((1 << 22) // 8 + 3, 8), ((3 << 21) // 8, 8), ((3 << 21) // 8 + 5, 8),
+                                 ((1 << 20) // 2 + 7, 2), ((1 << 22) // 32, 32)])
+def test_default_kernel_choice_boundaries(precision, T, D):
+    """With no kernel forced, sizes on either side of the boundaries where the default switches
+    between the row kernel (D fixed at compile time) and the pipelined kernel: the result is the
+    recursion, whichever kernel the size picks."""
+    keys = ("PMCMC_SCAN_KERNEL", "PMCMC_SCAN_SHAPE", "PMCMC_SCAN_DCONST", "PMCMC_PIPE_CTAS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ.pop(k, None)
+    try:
+        rng = np.random.default_rng(T * 3 + D)
+        a = rng.uniform(-0.98, 0.98, (T, D))
+        b = rng.standard_normal((T, D))
+        s = rng.standard_normal((T, D))
+        a_used, b_used, s_in, out = _run(precision, a, b, s)
+    finally:
+        for k, v in saved.items():
+            if v is not None:
+                os.environ[k] = v
+    delta = O.linear_recursion(a_used, b_used, dense=False)
+    np.testing.assert_allclose(out - s_in, delta, rtol=2e-5, atol=2e-4)
