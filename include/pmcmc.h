@@ -257,6 +257,23 @@ pmcmc_status pmcmc_scan(pmcmc_ctx *ctx, pmcmc_jac kind, pmcmc_precision precisio
                         const void *a, const void *b, void *s, void *stream);
 
 /*
+ * The kernel pmcmc_scan would run for a diagonal scan (kind PMCMC_JAC_DIAG) of T x D at
+ * `precision` with 16-byte-aligned a, b and s, computed on the host without device work (the
+ * same environment variables are read):
+ *   kernel_out     0 row kernel (D a run-time value), 1 row kernel with D fixed at compile time,
+ *                  2 register-resident kernel (one sub-chunk per warp), 3 staged bulk copies,
+ *                  4 pipelined bulk copies, 5 thread-block cluster, 6 shared-memory kernel (D > 32);
+ *   tile_out       timesteps per tile (per cluster tile for 5);
+ *   tiles_out      tiles of the launch;
+ *   max_tiles_out  tiles the look-back workspace of pmcmc_scan holds (a launch needs
+ *                  tiles_out <= max_tiles_out).
+ * PMCMC_EINVAL for T or D <= 0, a null output or an unknown precision; PMCMC_EUNSUPPORTED for
+ * another kind or D > 256.  Needs no context and no GPU.
+ */
+pmcmc_status pmcmc_scan_plan(pmcmc_jac kind, pmcmc_precision precision, int T, int D, int *kernel_out,
+                             int *tile_out, int *tiles_out, int *max_tiles_out);
+
+/*
  * Adjoint of a chain functional at the converged fixed point, with every accept decision held
  * (the chain is then a smooth function of the parameters).  Given dL/ds (T x D device reals)
  * it runs the transposed recursion backward,

@@ -20,7 +20,7 @@ __all__ = [
     "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan", "pmcmc_adjoint", "pmcmc_solve_batched",
     "pmcmc_solve_async", "result_from_device",
     "ChainDesc", "real_dtype", "loaded_library_path", "pmcmc_profile_enable",
-    "pmcmc_profile_get", "pmcmc_scan_noalloc", "ChainSolve", "solve_differentiable",
+    "pmcmc_profile_get", "pmcmc_scan_noalloc", "pmcmc_scan_plan", "ChainSolve", "solve_differentiable",
     "pmcmc_seq_solve_batched",
 ]
 
@@ -361,6 +361,22 @@ def pmcmc_seq_solve_batched(chains: list[ChainDesc], precision: str = "f32"):
     oc = Options(precision=precision).c()
     st = L.load().pmcmc_seq_solve_batched(ctx, len(chains), arr, C.byref(oc), _stream())
     _check(ctx, st)
+
+
+SCAN_PLAN_KERNELS = ("rows", "rows_const_d", "register", "staged", "pipe", "cluster", "wide")
+
+
+def pmcmc_scan_plan(precision: str, T: int, D: int) -> dict:
+    """The diagonal-scan kernel pmcmc_scan picks for T x D at `precision` (16-byte-aligned
+    buffers), its timesteps per tile, the tiles of the launch and the tiles its look-back
+    workspace holds.  Host-only: needs no GPU."""
+    k, tile, tiles, mt = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    st = L.load().pmcmc_scan_plan(JACS["diag"], PRECISIONS[precision], T, D, C.byref(k), C.byref(tile),
+                                  C.byref(tiles), C.byref(mt))
+    if st != L.PMCMC_OK:
+        raise PmcmcError(st, f"pmcmc_scan_plan: T={T}, D={D}, precision {precision}")
+    return {"kernel": SCAN_PLAN_KERNELS[k.value], "tile": tile.value, "tiles": tiles.value,
+            "max_tiles": mt.value}
 
 
 def pmcmc_profile_enable(enable: bool = True):

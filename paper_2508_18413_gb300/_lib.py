@@ -57,7 +57,7 @@ EXPORTS = [
     "pmcmc_options_default", "pmcmc_create", "pmcmc_destroy", "pmcmc_last_error",
     "pmcmc_gen_noise", "pmcmc_solve", "pmcmc_seq_solve", "pmcmc_linearize", "pmcmc_scan",
     "pmcmc_adjoint", "pmcmc_solve_batched", "pmcmc_profile_enable", "pmcmc_profile_get",
-    "pmcmc_scan_noalloc", "pmcmc_seq_solve_batched",
+    "pmcmc_scan_noalloc", "pmcmc_seq_solve_batched", "pmcmc_scan_plan",
 ]
 
 _lib = None
@@ -109,6 +109,9 @@ def load(path: str = LIB_PATH):
     lib.pmcmc_seq_solve_batched.restype = st
     lib.pmcmc_scan_noalloc.argtypes = [i, i, i, vp, vp, vp, vp]
     lib.pmcmc_scan_noalloc.restype = st
+    ip = C.POINTER(C.c_int)
+    lib.pmcmc_scan_plan.argtypes = [i, i, i, i, ip, ip, ip, ip]
+    lib.pmcmc_scan_plan.restype = st
     lib.pmcmc_profile_enable.argtypes = [vp, i]
     lib.pmcmc_profile_enable.restype = st
     lib.pmcmc_profile_get.argtypes = [vp, C.POINTER(pmcmc_profile)]

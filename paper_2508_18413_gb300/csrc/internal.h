@@ -39,6 +39,18 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
                              EvalStats *stats, const int *skip, unsigned int spin_limit,
                              cudaStream_t st);
 
+// The diagonal-scan kernel launch_scan_diag picks (a, b, s 16-byte aligned), without device work.
+enum ScanPlanKernel {
+    kPlanRows = 0,         // row kernel, D a run-time value
+    kPlanRowsConstD = 1,   // row kernel, D fixed at compile time
+    kPlanRegister = 2,     // register-resident kernel, one sub-chunk per warp
+    kPlanStaged = 3,       // bulk copies into shared memory
+    kPlanPipe = 4,         // persistent, double-buffered bulk copies
+    kPlanCluster = 5,      // tiles shared by a thread-block cluster
+    kPlanDiagWide = 6      // shared-memory staged kernel for D > 32
+};
+void plan_scan_diag(bool f64, int storage, int T, int D, int *kernel, int *tile, int *tiles);
+
 // Row kernel of the diagonal scan with D a compile-time constant (D a power of two up to 32,
 // 8 rows per warp, `nsub` sub-chunks per warp); kind 0: FP32, 1: FP32 with bfloat16 a and b,
 // 2: FP64.  cudaErrorInvalidValue for any other D or a tile count beyond the workspace.

@@ -980,6 +980,44 @@ cudaError_t launch_scan_diag(bool f64, int storage, int T, int D, int tile_t, co
     return run_scan_diag<float, float>(T, D, tile_t, a, b, s, s_reset, w, stats, skip, spin_limit, st);
 }
 
+// What launch_scan_diag runs for (T, D) with 16-byte-aligned a, b and s, computed from the same
+// helpers without device work: the kernel (ScanPlanKernel), its timesteps per tile and the
+// tiles of the launch.
+void plan_scan_diag(bool f64, int storage, int T, int D, int *kernel, int *tile, int *tiles) {
+    const int rb = f64 ? 8 : 4, sbytes = f64 ? 8 : (storage == 1 ? 2 : 4);
+    int k = kPlanDiagWide, tt = 0;
+    if (D > 32) {
+        tt = diag_scan_tile(T, D, rb);
+    } else {
+        const int choice = scan_kernel_choice((long long)T * D, D, f64, storage);
+        const int P = 32 / D;
+        if (choice == 3 && !f64) {
+            k = kPlanCluster;
+            tt = diag_scan_tile_cluster(D, sbytes);
+        } else if (choice == 2) {
+            k = kPlanPipe;
+            tt = 8 * P * pipe_run(T, D, sbytes, rb, pipe_ctas());
+        } else if (choice == 1) {
+            k = kPlanStaged;
+            tt = staged_tile(T, D, rb);
+        } else {
+            int rows, nsub;
+            diag_shape(T, D, &rows, &nsub);
+            tt = 8 * rows * nsub * P;
+            const char *dc = getenv("PMCMC_SCAN_DCONST");
+            if (nsub == 1)
+                k = kPlanRegister;
+            else if (rows == 8 && (D & (D - 1)) == 0 && !(dc && dc[0] == '0'))
+                k = kPlanRowsConstD;
+            else
+                k = kPlanRows;
+        }
+    }
+    *kernel = k;
+    *tile = tt;
+    *tiles = ceil_div(T, tt);
+}
+
 // ==========================================================================================
 // Dense scan (DEER, Eq. 3), D <= 32: one CTA per chunk of C timesteps.
 //   Phase A: chunk aggregate (Phi, beta) = composition of its (J_t, b_t), sequential matmuls.

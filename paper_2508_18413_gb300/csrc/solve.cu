@@ -319,6 +319,19 @@ pmcmc_status pmcmc_scan(pmcmc_ctx *c, pmcmc_jac kind, pmcmc_precision prec, int 
     return PMCMC_OK;
 }
 
+pmcmc_status pmcmc_scan_plan(pmcmc_jac kind, pmcmc_precision prec, int T, int D, int *kernel_out,
+                             int *tile_out, int *tiles_out, int *max_tiles_out) {
+    if (kind != PMCMC_JAC_DIAG) return PMCMC_EUNSUPPORTED;
+    if (T <= 0 || D <= 0 || !kernel_out || !tile_out || !tiles_out || !max_tiles_out) return PMCMC_EINVAL;
+    if (prec != PMCMC_F64 && prec != PMCMC_F32 && prec != PMCMC_F32_SCAN_BF16) return PMCMC_EINVAL;
+    if (D > 256) return PMCMC_EUNSUPPORTED;
+    const bool f64 = prec == PMCMC_F64;
+    plan_scan_diag(f64, prec == PMCMC_F32_SCAN_BF16 ? 1 : 0, T, D, kernel_out, tile_out, tiles_out);
+    // the look-back workspace pmcmc_scan reserves: one flag, aggregate and inclusive value per tile
+    *max_tiles_out = ceil_div(T, diag_scan_tile(T, D, f64 ? 8 : 4));
+    return PMCMC_OK;
+}
+
 }  // extern "C"
 
 // ==========================================================================================
